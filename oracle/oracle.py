@@ -1,0 +1,145 @@
+"""ctypes binding of the FP64 CPU oracle (oracle/p3_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the product path never imports this module.
+
+Conventions (P3DFFT paper, Sect. 3.2 and Table 1, with one process holding
+the whole grid):
+  real arrays     numpy float64  [Nz][Ny][Nx]          (X fastest)
+  complex arrays  numpy complex128 [Nz][Ny][H], H = Nx//2 + 1  (XYZ storage)
+  ZYX storage     [H][Ny][Nz] (the STRIDE1 Z-pencil of Table 1), produced here
+                  only by the trivial permutation to_zyx().
+Transform types per dimension: FFT, CHEB (DCT-I, third dimension only), EMPTY.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FFT, CHEB, EMPTY = 0, 1, 2
+
+_lib = None
+
+
+def nthreads_default() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return max(1, os.cpu_count() or 1)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    L, I, P = ctypes.c_long, ctypes.c_int, ctypes.c_void_p
+    lib.p3o_fft1d.argtypes = [L, P, P, I]
+    lib.p3o_dct1.argtypes = [L, P, P]
+    lib.p3o_x_r2c_rows.argtypes = [L, P, P, L, L, I]
+    lib.p3o_x_c2r_rows.argtypes = [L, P, P, L, L, I]
+    lib.p3o_c2c_lines.argtypes = [L, L, L, L, L, P, L, L, I, I]
+    lib.p3o_dct1_lines.argtypes = [L, L, L, L, L, P, L, L, I]
+    lib.p3o_forward.argtypes = [L, L, L, I, I, P, P, I]
+    lib.p3o_backward.argtypes = [L, L, L, I, I, P, P, I]
+    for name in ("p3o_fft1d", "p3o_dct1", "p3o_x_r2c_rows", "p3o_x_c2r_rows",
+                 "p3o_c2c_lines", "p3o_dct1_lines", "p3o_forward", "p3o_backward"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError("oracle %s failed with code %d" % (what, rc))
+
+
+def half(nx: int) -> int:
+    """H = floor(Nx/2) + 1 complex bins per X line (Sect. 3.2)."""
+    return nx // 2 + 1
+
+
+def scale(nx: int, ny: int, nz: int, ttypes=(FFT, FFT, FFT)) -> float:
+    """Round-trip factor of the unnormalised pair (Sect. 4.1 'apart from a
+    scale factor'): the product over dimensions of n for FFT, 2(n-1) for
+    Chebyshev (DCT-I applied twice) and 1 for the empty transform."""
+    s = float(nx)
+    for n, t in ((ny, ttypes[1]), (nz, ttypes[2])):
+        s *= {FFT: float(n), CHEB: 2.0 * (n - 1), EMPTY: 1.0}[t]
+    return s
+
+
+def fft1d(x, sign: int = -1) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.empty_like(x)
+    _check(_load().p3o_fft1d(x.size, _ptr(x), _ptr(out), sign), "fft1d")
+    return out
+
+
+def dct1(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.empty_like(x)
+    _check(_load().p3o_dct1(x.size, _ptr(x), _ptr(out)), "dct1")
+    return out
+
+
+def forward(f, ttypes=(FFT, FFT, FFT), nthreads: int = 0) -> np.ndarray:
+    """3D forward transform of a real [Nz][Ny][Nx] array -> [Nz][Ny][H]."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nz, ny, nx = f.shape
+    F = np.empty((nz, ny, half(nx)), dtype=np.complex128)
+    rc = _load().p3o_forward(nx, ny, nz, ttypes[1], ttypes[2], _ptr(f), _ptr(F),
+                             nthreads or nthreads_default())
+    _check(rc, "forward")
+    return F
+
+
+def backward(F, nx: int, ttypes=(FFT, FFT, FFT), nthreads: int = 0) -> np.ndarray:
+    """3D inverse transform of a complex [Nz][Ny][H] array -> real [Nz][Ny][Nx]."""
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    nz, ny, H = F.shape
+    if H != half(nx):
+        raise ValueError("complex array has %d bins per X line, expected %d" % (H, half(nx)))
+    f = np.empty((nz, ny, nx), dtype=np.float64)
+    rc = _load().p3o_backward(nx, ny, nz, ttypes[1], ttypes[2], _ptr(F), _ptr(f),
+                              nthreads or nthreads_default())
+    _check(rc, "backward")
+    return f
+
+
+def to_zyx(F) -> np.ndarray:
+    """XYZ [Nz][Ny][H] -> ZYX [H][Ny][Nz] (Table 1, STRIDE1 Z-pencil)."""
+    return np.ascontiguousarray(np.transpose(F, (2, 1, 0)))
+
+
+def from_zyx(G) -> np.ndarray:
+    """ZYX [H][Ny][Nz] -> XYZ [Nz][Ny][H]."""
+    return np.ascontiguousarray(np.transpose(G, (2, 1, 0)))
+
+
+# --- stage-level entry points (used for line-sampled checks and timing) ---
+
+def x_r2c_rows(nx, f_flat, F_flat, r0, r1, nthreads=0):
+    _check(_load().p3o_x_r2c_rows(nx, _ptr(f_flat), _ptr(F_flat), r0, r1,
+                                  nthreads or nthreads_default()), "x_r2c_rows")
+
+
+def x_c2r_rows(nx, F_flat, f_flat, r0, r1, nthreads=0):
+    _check(_load().p3o_x_c2r_rows(nx, _ptr(F_flat), _ptr(f_flat), r0, r1,
+                                  nthreads or nthreads_default()), "x_c2r_rows")
+
+
+def c2c_lines(n, per, gstride, lstride, es, data, l0, l1, sign, nthreads=0):
+    _check(_load().p3o_c2c_lines(n, per, gstride, lstride, es, _ptr(data), l0, l1,
+                                 sign, nthreads or nthreads_default()), "c2c_lines")
+
+
+def dct1_lines(n, per, gstride, lstride, es, data, l0, l1, nthreads=0):
+    _check(_load().p3o_dct1_lines(n, per, gstride, lstride, es, _ptr(data), l0, l1,
+                                  nthreads or nthreads_default()), "dct1_lines")
