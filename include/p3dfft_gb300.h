@@ -1,0 +1,163 @@
+/*
+ * p3dfft_gb300.h -- C ABI of a single-GPU (GB300, sm_103a) library for the
+ * 3D real-to-complex forward transform and its complex-to-real inverse, done
+ * the way the P3DFFT paper (Pekurovsky, "P3DFFT: a framework for parallel
+ * computations of Fourier transforms in three dimensions") describes: three
+ * stages of batched 1D transforms -- X (real-to-complex), Y (complex) and Z
+ * (complex FFT, Chebyshev or empty) -- with the paper's all-to-all
+ * re-orientations between pencils turned into on-device transposes fused into
+ * the stage kernels' loads and stores (Sect. 2, Fig. 2; Sect. 3.3).
+ *
+ * Conventions used by every call below.
+ *
+ * Arrays are C row-major with the rightmost index fastest; "dims" lists the
+ * extents fastest first, as the paper's Table 1 lists L1, L2, L3.
+ *   real input / output  (X-pencil, Table 1):   f[Nz][Ny][Nx]         dims {Nx, Ny, Nz}
+ *   complex half-spectrum, H = floor(Nx/2) + 1 bins per X line (Sect. 3.2):
+ *     P3_LAYOUT_XYZ  (STRIDE1 undefined):      F[Nz][Ny][H]          dims {H, Ny, Nz}
+ *     P3_LAYOUT_ZYX  (STRIDE1 defined):        F[H][Ny][Nz]          dims {Nz, Ny, H}
+ * Complex values are interleaved (re, im) pairs of the plan's precision.
+ *
+ * Transforms (Sect. 2, Sect. 3.1), both directions unnormalised:
+ *   forward  F[kz][ky][kx] = sum_{x,y,z} f * exp(-2 pi i (kx x/Nx + ky y/Ny + kz z/Nz)),
+ *            kx < H; a CHEB third dimension replaces the Z sum with the DCT-I
+ *            Y_n = x_0 + (-1)^n x_M + 2 sum_{j=1}^{M-1} x_j cos(pi j n / M), M = Nz-1
+ *            (real and imaginary parts alike; Gauss-Lobatto points
+ *            z_j = cos(pi j / M)); an EMPTY dimension is the identity.
+ *   inverse  the adjoint stages in reverse order with the + sign, the X stage
+ *            being f[x] = Re sum_{k<H} w_k F[k] exp(+2 pi i k x / Nx) with
+ *            w_0 = 1, w_{Nx/2} = 1 for even Nx, w_k = 2 otherwise (so the
+ *            imaginary parts of each line's DC and Nyquist bins are ignored).
+ *   A forward-inverse round trip returns the input times p3_plan_scale().
+ *
+ * Memory: every data pointer (inputs, outputs, workspace) is a caller-owned
+ * device pointer of the device that was current at p3_plan_create, 16-byte
+ * aligned.  The library allocates nothing per call; the plan owns only its
+ * small twiddle / chirp tables (one cudaMalloc at creation).
+ *
+ * Execution: ftran / btran enqueue kernels on `stream` (a cudaStream_t; NULL
+ * is the legacy default stream) and return without synchronising.  Inputs are
+ * never written.  Out-of-place only: an output that overlaps the input or the
+ * workspace is rejected.  A plan is immutable after creation (except for the
+ * optional timing events) and may be used from several threads with distinct
+ * workspaces.  No call throws, aborts or prints.
+ */
+#ifndef P3DFFT_GB300_H
+#define P3DFFT_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define P3_VERSION 1
+
+typedef struct p3_plan_s* p3_plan;
+
+typedef enum {
+    P3_OK = 0,
+    P3_ERR_INVALID = 1,     /* bad argument: NULL, misaligned, bad dims, overlap */
+    P3_ERR_UNSUPPORTED = 2, /* valid request outside what this build implements */
+    P3_ERR_NOMEM = 3,       /* host or device allocation at plan creation failed */
+    P3_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
+    P3_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    P3_ERR_WORKSPACE = 6    /* workspace required but NULL */
+} p3_status;
+
+/* Sect. 3.1: single and double precision. */
+typedef enum { P3_F32 = 0, P3_F64 = 1 } p3_precision;
+
+/* Sect. 3.1 / Sect. 5: Fourier, Chebyshev (DCT-I, third dimension only), empty. */
+typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2 } p3_ttype;
+
+/* Table 1: storage order of the Z-pencil complex array. */
+typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
+
+/*
+ * p3_plan_create -- build a plan for an Nx x Ny x Nz grid (Sect. 3.2: the
+ * user sets the grid size; the library keeps its internal variables hidden).
+ *   out        receives the plan handle (set to NULL on failure).
+ *   nx,ny,nz   grid extents, each >= 1; Nz >= 2 when ttype[2] == P3_CHEB.
+ *   prec       P3_F32 or P3_F64: the type of the data and of the arithmetic.
+ *   ttype      per-dimension transform; ttype[0] must be P3_FFT (the X
+ *              real-to-complex stage defines the path), ttype[1] P3_FFT or
+ *              P3_EMPTY, ttype[2] P3_FFT, P3_CHEB or P3_EMPTY.
+ *   out_layout storage order of the complex array (Table 1).
+ *   flags      must be 0.
+ * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
+ * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
+ * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.
+ * Errors: P3_ERR_INVALID (NULL out/ttype, bad dims or enum, flags != 0),
+ * P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA (no usable device).
+ * Argument checks happen before any CUDA call.
+ */
+p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec,
+                         const p3_ttype ttype[3], p3_layout out_layout, unsigned flags);
+
+/* Releases the plan and its device tables.  NULL is accepted.  The caller
+   must ensure no enqueued work still uses the plan. */
+p3_status p3_plan_destroy(p3_plan plan);
+
+/*
+ * p3_ftran_r2c -- forward transform (R2C: X-pencil input, Z-pencil output,
+ * Sect. 3.2).  in_real: Nx*Ny*Nz reals; out_cplx: H*Ny*Nz complex in the
+ * plan's layout; workspace: p3_plan_workspace_bytes() bytes (may be NULL
+ * when that is 0).  Errors: P3_ERR_INVALID (NULL plan/in/out, misaligned or
+ * overlapping buffers), P3_ERR_UNSUPPORTED (in == out), P3_ERR_WORKSPACE,
+ * P3_ERR_CUDA (launch failure; the stream state is then undefined).
+ */
+p3_status p3_ftran_r2c(p3_plan plan, const void* in_real, void* out_cplx,
+                       void* workspace, void* stream);
+
+/*
+ * p3_btran_c2r -- inverse transform (C2R: Z-pencil input in the plan's
+ * layout, X-pencil real output, Sect. 3.2).  in_cplx is not modified, which
+ * is why the inverse needs a workspace.  Same errors as p3_ftran_r2c.
+ */
+p3_status p3_btran_c2r(p3_plan plan, const void* in_cplx, void* out_real,
+                       void* workspace, void* stream);
+
+/* Extents of the real (X-pencil) and complex (Z-pencil) arrays, fastest
+   first, as in the header comment (Sect. 3.2 get-dimension routines). */
+p3_status p3_plan_get_dims(p3_plan plan, int in_dims[3], int out_dims[3]);
+
+/* Bytes of device workspace that ftran and btran need (the larger of the
+   two); 0 when neither needs any. */
+p3_status p3_plan_workspace_bytes(p3_plan plan, size_t* bytes);
+
+/* Round-trip factor: btran(ftran(f)) = scale * f, the product over the
+   dimensions of n (FFT), 2(n-1) (CHEB) or 1 (EMPTY) (Sect. 4.1). */
+p3_status p3_plan_scale(p3_plan plan, double* scale);
+
+/*
+ * Optional per-stage timing.  events: 8 cudaEvent_t handles (or NULL to turn
+ * timing off).  ftran records events[0] before its first stage kernel and
+ * events[i] after its i-th stage (i = 1..3); btran uses events[4..7] the same
+ * way.  A direction with fewer than three stages records the remaining events
+ * right after its last stage.  While events are set the plan must not be used
+ * from two threads at once.
+ */
+p3_status p3_plan_set_stage_events(p3_plan plan, void* const* events, int n_events);
+
+/*
+ * Writes a one-line-per-stage description of the plan (kernel, line length,
+ * radix sequence, lines per CTA, threads, shared memory, algorithmic bytes)
+ * into buf (always NUL-terminated when len > 0).  P3_ERR_INVALID on NULL.
+ */
+p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len);
+
+/* Number of kernel launches one ftran (dir = 0) or btran (dir = 1) makes. */
+p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
+
+/* Static string for a status code; never NULL. */
+const char* p3_status_string(p3_status s);
+
+/* P3_VERSION of the built library. */
+int p3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P3DFFT_GB300_H */

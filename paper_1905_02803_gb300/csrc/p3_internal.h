@@ -1,0 +1,77 @@
+// Internal declarations shared by the plan code (p3_plan.cu) and the stage
+// kernels (p3_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace p3 {
+
+// Largest radix sequence a line plan can hold (mixed 2/3/5/7 factorizations
+// of lengths <= 4096 have at most 12 prime factors).
+constexpr int kMaxPasses = 14;
+// Complex values each thread keeps in registers during a pass.
+constexpr int kVmax = 16;
+// Threads per CTA never exceed this (matches __launch_bounds__).
+constexpr int kMaxThreads = 256;
+// Longest native line; Bluestein lines need a padded length <= this too.
+constexpr int kMaxLine = 4096;
+
+// Line L, element e of a strided batch lives at
+//   (L / per) * gstride + (L % per) * lstride + e * es
+// counted in elements of the array's type (real or complex).
+struct LineMap {
+    long long per, gstride, lstride, es;
+};
+
+enum StageOp : int {
+    OP_C2C = 0,       // complex line -> complex line
+    OP_R2C_HALF = 1,  // even Nx: length Nx/2 complex FFT of (f[2j], f[2j+1]) + real split
+    OP_R2C_FULL = 2,  // odd Nx: complex FFT of the real line, keep H bins
+    OP_C2R_HALF = 3,  // even Nx: Hermitian pre-twiddle + length Nx/2 complex FFT
+    OP_C2R_FULL = 4,  // odd Nx: weighted, zero-padded line, complex FFT, real part
+    OP_DCT1 = 5,      // Chebyshev: even extension to 2M points, FFT, first M+1 bins
+    OP_COPY = 6,      // empty transform (re-orientation only)
+};
+
+// Everything one stage kernel launch needs (passed by value).
+struct StageArgs {
+    const void* src;
+    void* dst;
+    LineMap in, out;
+    long long nlines;
+    int op;
+    int n_in, n_out;   // points read / written per line
+    int nfft;          // length of the complex DFT done on each line
+    int sign;          // -1 forward, +1 inverse
+    int B;             // lines per CTA (power of two)
+    int LDB;           // shared-memory pitch between consecutive elements of a line
+    int tpl;           // threads per line
+    int in_elem_fast;  // 1: global input has es == 1 (lanes walk elements)
+    int out_elem_fast; // 1: global output has es == 1
+    // native Stockham passes over nfft points
+    int npass;
+    int rad[kMaxPasses];
+    const void* tw;    // tw[k] = exp(-2 pi i k / twn), complex of the stage type
+    int twn;
+    const void* tw2;   // real-split twiddles exp(-2 pi i k / Nx) (R2C/C2R_HALF), length Nx
+    // Bluestein (nfft not 7-smooth): DFT_nfft via padded length m
+    int blue;
+    int m;
+    int mpass;
+    int mrad[kMaxPasses];
+    const void* chirp; // c[j] = exp(-pi i j^2 / nfft), j < nfft
+    const void* bhat;  // DFT_m of the conjugate chirp filter, pre-scaled by 1/m
+    const void* twm;   // exp(-2 pi i k / m), k < m
+    size_t smem;       // dynamic shared memory bytes
+    int threads;       // B * tpl
+};
+
+// Launch one stage (defined in p3_kernels.cu).  Returns the launch error.
+cudaError_t launch_stage_f32(const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_f64(const StageArgs& a, cudaStream_t s);
+// One-time kernel attribute set-up for the current device (max dynamic smem).
+cudaError_t prepare_kernels();
+
+}  // namespace p3

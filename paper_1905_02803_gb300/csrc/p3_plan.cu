@@ -1,0 +1,675 @@
+// Plan construction and the C ABI (include/p3dfft_gb300.h).
+//
+// A plan fixes, for each direction, the sequence of stage launches of the
+// P3DFFT method (Sect. 2, Fig. 2): X real-to-complex, Y complex, Z complex /
+// Chebyshev / empty, each a batched 1D transform over every line of the
+// volume, and the buffers each stage reads and writes.  The paper's
+// pencil re-orientations (Sect. 3.3) become the stage kernels' load and store
+// addressing; the STRIDE1 Z-pencil layout (ZYX, Table 1) is produced by the
+// Z stage's store and consumed by the inverse Z stage's load.
+//
+// The host builds every table in FP64 (roots of unity by exact integer
+// reduction of the angle to an octant, Bluestein chirps with j^2 reduced mod
+// 2n in integers) and rounds it once to the plan's precision.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <complex>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/p3dfft_gb300.h"
+#include "p3_internal.h"
+
+using p3::LineMap;
+using p3::StageArgs;
+
+namespace {
+
+enum Buf { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
+
+struct Stage {
+    StageArgs a;
+    int src, dst;       // Buf roles
+    const char* name;
+    double bytes;       // algorithmic HBM bytes of one launch
+};
+
+struct TableKey {
+    int kind;  // 0 roots, 1 chirp, 2 bhat
+    long long n, m;
+    bool operator<(const TableKey& o) const
+    {
+        if (kind != o.kind) return kind < o.kind;
+        if (n != o.n) return n < o.n;
+        return m < o.m;
+    }
+};
+
+}  // namespace
+
+struct p3_plan_s {
+    int nx, ny, nz, H;
+    p3_precision prec;
+    p3_ttype tt[3];
+    p3_layout layout;
+    int device;
+    size_t csize;  // bytes per complex element
+    void* dtab;
+    std::vector<Stage> st[2];
+    size_t ws_bytes;
+    double scale;
+    void* events[8];
+    bool timing;
+    std::string desc;
+};
+
+namespace {
+
+const long double kPi = 3.141592653589793238462643383279502884L;
+
+// exp(-2 pi i k / n) in FP64: the angle is reduced exactly to octant o and an
+// offset x in [0, pi/4] before cosl/sinl, then rotated back by symmetry.
+std::complex<double> unit_root(long long k, long long n)
+{
+    k %= n;
+    if (k < 0) k += n;
+    const long long o = (8 * k) / n;
+    const long long r = 8 * k - o * n;  // angle = (pi/4) (o + r/n)
+    long double c, s;                   // cos / sin of the angle
+    if ((o & 1) == 0) {
+        const long double x = (kPi / 4) * (long double)r / (long double)n;
+        const long double cx = cosl(x), sx = sinl(x);
+        switch (o / 2) {
+        case 0: c = cx; s = sx; break;
+        case 1: c = -sx; s = cx; break;
+        case 2: c = -cx; s = -sx; break;
+        default: c = sx; s = -cx; break;
+        }
+    } else {
+        const long double y = (kPi / 4) * (long double)(n - r) / (long double)n;  // (o+1) pi/4 - angle
+        const long double cy = cosl(y), sy = sinl(y);
+        switch ((o + 1) / 2) {
+        case 1: c = sy; s = cy; break;
+        case 2: c = -cy; s = sy; break;
+        case 3: c = -sy; s = -cy; break;
+        default: c = cy; s = -sy; break;
+        }
+    }
+    return std::complex<double>((double)c, -(double)s);
+}
+
+// In-place iterative radix-2 DFT (exp(-2 pi i ...)) in long double, for the
+// Bluestein filter spectrum at plan time; m is a power of two.
+void host_dft_pow2(std::vector<std::complex<long double>>& a)
+{
+    const size_t m = a.size();
+    for (size_t i = 1, j = 0; i < m; ++i) {
+        size_t bit = m >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= m; len <<= 1) {
+        for (size_t i = 0; i < m; i += len) {
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w = unit_root((long long)k, (long long)len);
+                const std::complex<long double> wl((long double)w.real(), (long double)w.imag());
+                const std::complex<long double> u = a[i + k], v = a[i + k + len / 2] * wl;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+// Radix sequence for n (16s first, then 8/4/2, then 3, 5, 7).  Returns false
+// when n has a prime factor above 7.
+bool factor(int n, std::vector<int>& rad)
+{
+    rad.clear();
+    int m = n;
+    while (m % 16 == 0) { rad.push_back(16); m /= 16; }
+    if (m % 8 == 0) { rad.push_back(8); m /= 8; }
+    if (m % 4 == 0) { rad.push_back(4); m /= 4; }
+    if (m % 2 == 0) { rad.push_back(2); m /= 2; }
+    for (int p : {3, 5, 7})
+        while (m % p == 0) { rad.push_back(p); m /= p; }
+    return m == 1 && (int)rad.size() <= p3::kMaxPasses;
+}
+
+// Threads per line so that no thread holds more than kVmax values in a pass.
+int threads_per_line(int n, const std::vector<int>& rad)
+{
+    int tpl = 1;
+    for (int R : rad) {
+        const int nb = n / R, bm = p3::kVmax / R;
+        const int need = (nb + bm - 1) / bm;
+        if (need > tpl) tpl = need;
+    }
+    return tpl;
+}
+
+int pow2_floor(long long v)
+{
+    int p = 1;
+    while ((long long)p * 2 <= v) p *= 2;
+    return p;
+}
+
+long long pow2_ceil(long long v)
+{
+    long long p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
+
+struct TableSet {
+    std::map<TableKey, size_t> offs;  // byte offsets into the device block
+    std::vector<std::complex<double>> vals;
+    size_t add(const TableKey& k, std::vector<std::complex<double>>&& v)
+    {
+        auto it = offs.find(k);
+        if (it != offs.end()) return it->second;
+        const size_t off = vals.size();
+        vals.insert(vals.end(), v.begin(), v.end());
+        offs[k] = off;
+        return off;
+    }
+};
+
+size_t roots_table(TableSet& T, long long n)
+{
+    std::vector<std::complex<double>> v((size_t)n);
+    for (long long k = 0; k < n; ++k) v[(size_t)k] = unit_root(k, n);
+    return T.add(TableKey{0, n, 0}, std::move(v));
+}
+
+size_t chirp_table(TableSet& T, long long n)
+{
+    std::vector<std::complex<double>> v((size_t)n);
+    for (long long j = 0; j < n; ++j) v[(size_t)j] = unit_root((j * j) % (2 * n), 2 * n);
+    return T.add(TableKey{1, n, 0}, std::move(v));
+}
+
+size_t bhat_table(TableSet& T, long long n, long long m)
+{
+    std::vector<std::complex<long double>> b((size_t)m, std::complex<long double>(0, 0));
+    for (long long j = 0; j < n; ++j) {
+        const std::complex<double> c = std::conj(unit_root((j * j) % (2 * n), 2 * n));
+        const std::complex<long double> cl((long double)c.real(), (long double)c.imag());
+        b[(size_t)j] = cl;
+        if (j) b[(size_t)(m - j)] = cl;
+    }
+    host_dft_pow2(b);
+    std::vector<std::complex<double>> v((size_t)m);
+    for (long long k = 0; k < m; ++k)
+        v[(size_t)k] = std::complex<double>((double)(b[(size_t)k].real() / m), (double)(b[(size_t)k].imag() / m));
+    return T.add(TableKey{2, n, m}, std::move(v));
+}
+
+// Pointer-valued table fields hold byte offsets (+1, 0 = none) until the
+// device block exists.
+struct Pending {
+    size_t tw = 0, tw2 = 0, chirp = 0, bhat = 0, twm = 0;
+};
+
+// Line-FFT set-up: native radices over nfft, else Bluestein over m.
+// Returns P3_ERR_UNSUPPORTED for lines beyond the shared-memory limit.
+p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
+{
+    std::vector<int> rad;
+    a.blue = 0;
+    a.npass = 0;
+    a.mpass = 0;
+    a.m = 0;
+    if (a.nfft <= 1) {
+        a.tpl = 1;
+        return P3_OK;
+    }
+    if (factor(a.nfft, rad)) {
+        if (a.nfft > p3::kMaxLine) return P3_ERR_UNSUPPORTED;
+        a.npass = (int)rad.size();
+        for (int i = 0; i < a.npass; ++i) a.rad[i] = rad[i];
+        a.tpl = threads_per_line(a.nfft, rad);
+        if (a.tpl > p3::kMaxThreads) return P3_ERR_UNSUPPORTED;
+        a.twn = twn_native;
+        pend.tw = roots_table(T, twn_native) + 1;
+        return P3_OK;
+    }
+    const long long m = pow2_ceil(2LL * a.nfft - 1);
+    if (m > p3::kMaxLine) return P3_ERR_UNSUPPORTED;
+    factor((int)m, rad);
+    a.blue = 1;
+    a.m = (int)m;
+    a.mpass = (int)rad.size();
+    for (int i = 0; i < a.mpass; ++i) a.mrad[i] = rad[i];
+    a.tpl = threads_per_line((int)m, rad);
+    if (a.tpl > p3::kMaxThreads) return P3_ERR_UNSUPPORTED;
+    pend.chirp = chirp_table(T, a.nfft) + 1;
+    pend.bhat = bhat_table(T, a.nfft, m) + 1;
+    pend.twm = roots_table(T, m) + 1;
+    return P3_OK;
+}
+
+// Lines per CTA, pitch, threads and shared memory of a stage.
+void tile_setup(StageArgs& a, size_t csize)
+{
+    const int len = a.blue ? a.m : (a.nfft > 0 ? a.nfft : 1);
+    const bool elem = a.in_elem_fast || a.out_elem_fast;
+    const size_t cap = 96 * 1024;
+    int B = pow2_floor(p3::kMaxThreads / a.tpl);
+    if (B < 1) B = 1;
+    while (B > 1 && (size_t)len * (size_t)(B + 1) * csize > cap) B /= 2;
+    const long long lim = pow2_ceil(a.nlines > 0 ? a.nlines : 1);
+    if (B > lim) B = (int)lim;
+    a.B = B;
+    a.LDB = (elem && (B % 2 == 0)) ? B + 1 : B;
+    int th = B * a.tpl;
+    th = (th + 31) / 32 * 32;
+    a.threads = th;
+    a.smem = (size_t)len * (size_t)a.LDB * csize;
+}
+
+LineMap rows(long long nlines, long long pitch) { return LineMap{nlines > 0 ? nlines : 1, 0, pitch, 1}; }
+
+const char* op_name(int op)
+{
+    switch (op) {
+    case p3::OP_C2C: return "c2c";
+    case p3::OP_R2C_HALF: return "r2c_half";
+    case p3::OP_R2C_FULL: return "r2c_full";
+    case p3::OP_C2R_HALF: return "c2r_half";
+    case p3::OP_C2R_FULL: return "c2r_full";
+    case p3::OP_DCT1: return "dct1";
+    default: return "copy";
+    }
+}
+
+bool smooth_or_small(int n)
+{
+    std::vector<int> r;
+    if (n <= 1) return true;
+    if (factor(n, r)) return n <= p3::kMaxLine;
+    return pow2_ceil(2LL * n - 1) <= p3::kMaxLine;
+}
+
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* p3_status_string(p3_status s)
+{
+    switch (s) {
+    case P3_OK: return "ok";
+    case P3_ERR_INVALID: return "invalid argument";
+    case P3_ERR_UNSUPPORTED: return "unsupported";
+    case P3_ERR_NOMEM: return "out of memory";
+    case P3_ERR_CUDA: return "CUDA error";
+    case P3_ERR_TIMEOUT: return "device wait timed out";
+    case P3_ERR_WORKSPACE: return "workspace required";
+    default: return "unknown status";
+    }
+}
+
+int p3_version(void) { return P3_VERSION; }
+
+p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec, const p3_ttype ttype[3],
+                         p3_layout out_layout, unsigned flags)
+{
+    if (!out) return P3_ERR_INVALID;
+    *out = NULL;
+    if (!ttype || nx < 1 || ny < 1 || nz < 1 || flags != 0) return P3_ERR_INVALID;
+    if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
+    if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
+    for (int d = 0; d < 3; ++d)
+        if (ttype[d] != P3_FFT && ttype[d] != P3_CHEB && ttype[d] != P3_EMPTY) return P3_ERR_INVALID;
+    if (ttype[0] != P3_FFT) return P3_ERR_UNSUPPORTED;
+    if (ttype[1] == P3_CHEB) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_CHEB && nz < 2) return P3_ERR_INVALID;
+    // per-line length limits
+    if (!smooth_or_small(nx % 2 == 0 ? nx / 2 : nx)) return P3_ERR_UNSUPPORTED;
+    if (ttype[1] == P3_FFT && !smooth_or_small(ny)) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_FFT && !smooth_or_small(nz)) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_CHEB && !smooth_or_small(2 * (nz - 1))) return P3_ERR_UNSUPPORTED;
+
+    p3_plan P = new (std::nothrow) p3_plan_s();
+    if (!P) return P3_ERR_NOMEM;
+    P->nx = nx; P->ny = ny; P->nz = nz; P->H = nx / 2 + 1;
+    P->prec = prec;
+    for (int d = 0; d < 3; ++d) P->tt[d] = ttype[d];
+    P->layout = out_layout;
+    P->csize = prec == P3_F32 ? 8 : 16;
+    P->dtab = NULL;
+    P->timing = false;
+    memset(P->events, 0, sizeof(P->events));
+    const long long H = P->H, NY = ny, NZ = nz, NX = nx;
+    const size_t e = P->csize / 2;
+    const double creal = (double)e * NX * NY * NZ;        // bytes of the real array
+    const double ccplx = (double)P->csize * H * NY * NZ;  // bytes of the complex array
+
+    P->scale = (double)nx;
+    P->scale *= ttype[1] == P3_FFT ? (double)ny : 1.0;
+    P->scale *= ttype[2] == P3_FFT ? (double)nz : (ttype[2] == P3_CHEB ? 2.0 * (nz - 1) : 1.0);
+
+    TableSet T;
+    std::vector<Pending> pend[2];
+    p3_status rc = P3_OK;
+
+    const LineMap mapY = LineMap{H, NY * H, 1, H};
+    const LineMap mapZxyz = LineMap{H * NY, 0, 1, NY * H};
+    const LineMap mapZzyx = LineMap{H, NZ, NY * NZ, 1};
+    const bool zyx = out_layout == P3_LAYOUT_ZYX;
+
+    auto base_args = [&](int op, int n_in, int n_out, int nfft, int sign, long long nlines, LineMap in,
+                         LineMap outm) {
+        StageArgs a;
+        memset(&a, 0, sizeof(a));
+        a.op = op; a.n_in = n_in; a.n_out = n_out; a.nfft = nfft; a.sign = sign;
+        a.nlines = nlines; a.in = in; a.out = outm;
+        a.in_elem_fast = in.es == 1;
+        a.out_elem_fast = outm.es == 1;
+        return a;
+    };
+    auto push = [&](int dir, StageArgs a, int src, int dst, const char* name, double bytes, int twn) {
+        Pending pd;
+        if (rc != P3_OK) return;
+        if (a.op == p3::OP_R2C_HALF || a.op == p3::OP_C2R_HALF) {
+            pd.tw2 = roots_table(T, NX) + 1;
+        }
+        if (a.op != p3::OP_COPY) {
+            rc = line_setup(a, pd, T, twn);
+            if (rc != P3_OK) return;
+        } else {
+            a.tpl = 1;
+            a.nfft = a.n_in;  // slots per line; no FFT passes
+            a.npass = 0;
+        }
+        tile_setup(a, P->csize);
+        Stage s;
+        s.a = a; s.src = src; s.dst = dst; s.name = name; s.bytes = bytes;
+        P->st[dir].push_back(s);
+        pend[dir].push_back(pd);
+    };
+
+    // ---- forward: X r2c, Y c2c, Z c2c / DCT-I / re-orientation ----------
+    {
+        const bool half = nx % 2 == 0;
+        const int nfft = half ? nx / 2 : nx;
+        StageArgs a = base_args(half ? p3::OP_R2C_HALF : p3::OP_R2C_FULL, nx, (int)H, nfft, -1, NY * NZ,
+                                rows(NY * NZ, NX), rows(NY * NZ, H));
+        push(0, a, BUF_IN, zyx ? BUF_WS : BUF_OUT, "x_r2c", creal + ccplx, half ? nx : nx);
+        const int work = zyx ? BUF_WS : BUF_OUT;
+        if (ttype[1] == P3_FFT && ny > 1) {
+            a = base_args(p3::OP_C2C, ny, ny, ny, -1, H * NZ, mapY, mapY);
+            push(0, a, work, work, "y_c2c", 2 * ccplx, ny);
+        }
+        const LineMap zout = zyx ? mapZzyx : mapZxyz;
+        if (ttype[2] == P3_FFT && nz > 1) {
+            a = base_args(p3::OP_C2C, nz, nz, nz, -1, H * NY, mapZxyz, zout);
+            push(0, a, work, BUF_OUT, zyx ? "z_c2c_zyx" : "z_c2c", 2 * ccplx, nz);
+        } else if (ttype[2] == P3_CHEB) {
+            a = base_args(p3::OP_DCT1, nz, nz, 2 * (nz - 1), -1, H * NY, mapZxyz, zout);
+            push(0, a, work, BUF_OUT, zyx ? "z_dct1_zyx" : "z_dct1", 2 * ccplx, 2 * (nz - 1));
+        } else if (zyx) {
+            a = base_args(p3::OP_COPY, nz, nz, 1, -1, H * NY, mapZxyz, zout);
+            push(0, a, work, BUF_OUT, "z_copy_zyx", 2 * ccplx, 1);
+        }
+    }
+    // ---- inverse: Z, Y, X c2r -------------------------------------------
+    {
+        int cur = BUF_IN;
+        const LineMap zin = zyx ? mapZzyx : mapZxyz;
+        StageArgs a;
+        if (ttype[2] == P3_FFT && nz > 1) {
+            a = base_args(p3::OP_C2C, nz, nz, nz, +1, H * NY, zin, mapZxyz);
+            push(1, a, cur, BUF_WS, zyx ? "z_c2c_zyx_inv" : "z_c2c_inv", 2 * ccplx, nz);
+            cur = BUF_WS;
+        } else if (ttype[2] == P3_CHEB) {
+            a = base_args(p3::OP_DCT1, nz, nz, 2 * (nz - 1), +1, H * NY, zin, mapZxyz);
+            push(1, a, cur, BUF_WS, zyx ? "z_dct1_zyx_inv" : "z_dct1_inv", 2 * ccplx, 2 * (nz - 1));
+            cur = BUF_WS;
+        } else if (zyx) {
+            a = base_args(p3::OP_COPY, nz, nz, 1, +1, H * NY, zin, mapZxyz);
+            push(1, a, cur, BUF_WS, "z_copy_zyx_inv", 2 * ccplx, 1);
+            cur = BUF_WS;
+        }
+        if (ttype[1] == P3_FFT && ny > 1) {
+            a = base_args(p3::OP_C2C, ny, ny, ny, +1, H * NZ, mapY, mapY);
+            push(1, a, cur, BUF_WS, "y_c2c_inv", 2 * ccplx, ny);
+            cur = BUF_WS;
+        }
+        const bool half = nx % 2 == 0;
+        const int nfft = half ? nx / 2 : nx;
+        a = base_args(half ? p3::OP_C2R_HALF : p3::OP_C2R_FULL, (int)H, half ? nfft : nx, nfft, +1, NY * NZ,
+                      rows(NY * NZ, H), rows(NY * NZ, NX));
+        push(1, a, cur, BUF_OUT, "x_c2r", creal + ccplx, nx);
+    }
+    if (rc != P3_OK) {
+        delete P;
+        return rc;
+    }
+    bool need_ws = false;
+    for (int d = 0; d < 2; ++d)
+        for (auto& s : P->st[d])
+            if (s.src == BUF_WS || s.dst == BUF_WS) need_ws = true;
+    P->ws_bytes = need_ws ? (size_t)P->csize * (size_t)H * (size_t)NY * (size_t)NZ : 0;
+
+    // ---- device tables ------------------------------------------------------
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return P3_ERR_CUDA;
+    }
+    if (p3::prepare_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return P3_ERR_CUDA;
+    }
+    const size_t nvals = T.vals.size();
+    const size_t bytes = nvals * P->csize;
+    if (bytes) {
+        std::vector<unsigned char> host(bytes);
+        for (size_t i = 0; i < nvals; ++i) {
+            if (prec == P3_F32) {
+                float v[2] = {(float)T.vals[i].real(), (float)T.vals[i].imag()};
+                memcpy(&host[i * 8], v, 8);
+            } else {
+                double v[2] = {T.vals[i].real(), T.vals[i].imag()};
+                memcpy(&host[i * 16], v, 16);
+            }
+        }
+        cudaError_t ce = cudaMalloc(&P->dtab, bytes);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            delete P;
+            return ce == cudaErrorMemoryAllocation ? P3_ERR_NOMEM : P3_ERR_CUDA;
+        }
+        ce = cudaMemcpy(P->dtab, host.data(), bytes, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            cudaFree(P->dtab);
+            delete P;
+            return P3_ERR_CUDA;
+        }
+    }
+    auto resolve = [&](size_t off) -> const void* {
+        return off ? (const void*)((const unsigned char*)P->dtab + (off - 1) * P->csize) : NULL;
+    };
+    for (int d = 0; d < 2; ++d) {
+        for (size_t i = 0; i < P->st[d].size(); ++i) {
+            StageArgs& a = P->st[d][i].a;
+            const Pending& pd = pend[d][i];
+            a.tw = resolve(pd.tw);
+            a.tw2 = resolve(pd.tw2);
+            a.chirp = resolve(pd.chirp);
+            a.bhat = resolve(pd.bhat);
+            a.twm = resolve(pd.twm);
+        }
+    }
+    // ---- description ----------------------------------------------------------
+    char line[512];
+    for (int d = 0; d < 2; ++d) {
+        for (auto& s : P->st[d]) {
+            const StageArgs& a = s.a;
+            std::string rs;
+            const int np = a.blue ? a.mpass : a.npass;
+            for (int i = 0; i < np; ++i) {
+                rs += std::to_string(a.blue ? a.mrad[i] : a.rad[i]);
+                if (i + 1 < np) rs += "x";
+            }
+            if (rs.empty()) rs = "-";
+            snprintf(line, sizeof(line),
+                     "%s %s op=%s nfft=%d%s radices=%s lines=%lld B=%d LDB=%d tpl=%d threads=%d smem=%zu "
+                     "bytes=%.0f\n",
+                     d == 0 ? "fwd" : "bwd", s.name, op_name(a.op), a.nfft,
+                     a.blue ? (" bluestein_m=" + std::to_string(a.m)).c_str() : "", rs.c_str(), a.nlines, a.B,
+                     a.LDB, a.tpl, a.threads, a.smem, s.bytes);
+            P->desc += line;
+        }
+    }
+    *out = P;
+    return P3_OK;
+}
+
+p3_status p3_plan_destroy(p3_plan plan)
+{
+    if (!plan) return P3_OK;
+    if (plan->dtab) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != plan->device) cudaSetDevice(plan->device);
+        cudaFree(plan->dtab);
+        if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+        cudaGetLastError();
+    }
+    delete plan;
+    return P3_OK;
+}
+
+static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, void* stream)
+{
+    if (!P || !in || !out) return P3_ERR_INVALID;
+    if (!aligned16(in) || !aligned16(out) || (ws && !aligned16(ws))) return P3_ERR_INVALID;
+    if (in == out) return P3_ERR_UNSUPPORTED;
+    const size_t nreal = (size_t)P->nx * P->ny * P->nz * (P->csize / 2);
+    const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
+    const size_t nin = dir == 0 ? nreal : ncplx, nout = dir == 0 ? ncplx : nreal;
+    if (overlap(in, nin, out, nout)) return P3_ERR_INVALID;
+    bool uses_ws = false;
+    for (auto& s : P->st[dir])
+        if (s.src == BUF_WS || s.dst == BUF_WS) uses_ws = true;
+    if (uses_ws) {
+        if (!ws) return P3_ERR_WORKSPACE;
+        if (overlap(ws, P->ws_bytes, in, nin) || overlap(ws, P->ws_bytes, out, nout)) return P3_ERR_INVALID;
+    }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return P3_ERR_CUDA;
+    }
+    if (cur != P->device) return P3_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* const bufs[3] = {const_cast<void*>(in), out, ws};
+    cudaEvent_t* ev = P->timing ? (cudaEvent_t*)&P->events[dir * 4] : NULL;
+    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return P3_ERR_CUDA;
+    int i = 0;
+    for (auto& st : P->st[dir]) {
+        StageArgs a = st.a;
+        a.src = bufs[st.src];
+        a.dst = bufs[st.dst];
+        const cudaError_t e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
+        if (e != cudaSuccess) return P3_ERR_CUDA;
+        ++i;
+        if (ev && i <= 3 && cudaEventRecord(ev[i], s) != cudaSuccess) return P3_ERR_CUDA;
+    }
+    if (ev)
+        for (int k = i + 1; k <= 3; ++k)
+            if (cudaEventRecord(ev[k], s) != cudaSuccess) return P3_ERR_CUDA;
+    return P3_OK;
+}
+
+p3_status p3_ftran_r2c(p3_plan plan, const void* in_real, void* out_cplx, void* workspace, void* stream)
+{
+    return run(plan, 0, in_real, out_cplx, workspace, stream);
+}
+
+p3_status p3_btran_c2r(p3_plan plan, const void* in_cplx, void* out_real, void* workspace, void* stream)
+{
+    return run(plan, 1, in_cplx, out_real, workspace, stream);
+}
+
+p3_status p3_plan_get_dims(p3_plan plan, int in_dims[3], int out_dims[3])
+{
+    if (!plan || !in_dims || !out_dims) return P3_ERR_INVALID;
+    in_dims[0] = plan->nx; in_dims[1] = plan->ny; in_dims[2] = plan->nz;
+    if (plan->layout == P3_LAYOUT_XYZ) {
+        out_dims[0] = plan->H; out_dims[1] = plan->ny; out_dims[2] = plan->nz;
+    } else {
+        out_dims[0] = plan->nz; out_dims[1] = plan->ny; out_dims[2] = plan->H;
+    }
+    return P3_OK;
+}
+
+p3_status p3_plan_workspace_bytes(p3_plan plan, size_t* bytes)
+{
+    if (!plan || !bytes) return P3_ERR_INVALID;
+    *bytes = plan->ws_bytes;
+    return P3_OK;
+}
+
+p3_status p3_plan_scale(p3_plan plan, double* scale)
+{
+    if (!plan || !scale) return P3_ERR_INVALID;
+    *scale = plan->scale;
+    return P3_OK;
+}
+
+p3_status p3_plan_set_stage_events(p3_plan plan, void* const* events, int n_events)
+{
+    if (!plan) return P3_ERR_INVALID;
+    if (!events) {
+        plan->timing = false;
+        memset(plan->events, 0, sizeof(plan->events));
+        return P3_OK;
+    }
+    if (n_events != 8) return P3_ERR_INVALID;
+    for (int i = 0; i < 8; ++i)
+        if (!events[i]) return P3_ERR_INVALID;
+    for (int i = 0; i < 8; ++i) plan->events[i] = events[i];
+    plan->timing = true;
+    return P3_OK;
+}
+
+p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len)
+{
+    if (!plan || !buf) return P3_ERR_INVALID;
+    if (len == 0) return P3_OK;
+    const size_t n = plan->desc.size() < len - 1 ? plan->desc.size() : len - 1;
+    memcpy(buf, plan->desc.data(), n);
+    buf[n] = 0;
+    return P3_OK;
+}
+
+p3_status p3_plan_launches(p3_plan plan, int dir, int* launches)
+{
+    if (!plan || !launches || (dir != 0 && dir != 1)) return P3_ERR_INVALID;
+    *launches = (int)plan->st[dir].size();
+    return P3_OK;
+}
+
+}  // extern "C"

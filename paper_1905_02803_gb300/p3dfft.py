@@ -1,0 +1,233 @@
+"""ctypes binding of libp3dfft_gb300.so (include/p3dfft_gb300.h).
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels.  The functions keep the C names; `Plan` wraps them for torch
+tensors (device memory and streams come from PyTorch).  If the library has
+not been built, the first call raises: there is no other implementation to
+fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libp3dfft_gb300.so")
+
+P3_OK, P3_ERR_INVALID, P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA, P3_ERR_TIMEOUT, P3_ERR_WORKSPACE = range(7)
+P3_F32, P3_F64 = 0, 1
+P3_FFT, P3_CHEB, P3_EMPTY = 0, 1, 2
+P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
+
+EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_plan_get_dims",
+           "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
+           "p3_plan_launches", "p3_status_string", "p3_version")
+
+_lib = None
+
+
+class P3Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, p3_status_string(status), status))
+
+
+def load():
+    """Load the library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libp3dfft_gb300.so is not built (%s); run "
+                           "paper_1905_02803_gb300.build.build() first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    I, U, P, D = ctypes.c_int, ctypes.c_uint, ctypes.c_void_p, ctypes.c_double
+    lib.p3_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, I, ctypes.POINTER(I), I, U]
+    lib.p3_plan_destroy.argtypes = [P]
+    lib.p3_ftran_r2c.argtypes = [P, P, P, P, P]
+    lib.p3_btran_c2r.argtypes = [P, P, P, P, P]
+    lib.p3_plan_get_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.p3_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.p3_plan_scale.argtypes = [P, ctypes.POINTER(D)]
+    lib.p3_plan_set_stage_events.argtypes = [P, ctypes.POINTER(P), I]
+    lib.p3_plan_describe.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.p3_plan_launches.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.p3_status_string.argtypes = [I]
+    lib.p3_status_string.restype = ctypes.c_char_p
+    lib.p3_version.argtypes = []
+    for name in EXPORTS:
+        if name not in ("p3_status_string",):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != P3_OK:
+        raise P3Error(st, what)
+
+
+def p3_status_string(status: int) -> str:
+    return load().p3_status_string(int(status)).decode()
+
+
+def p3_version() -> int:
+    return load().p3_version()
+
+
+def p3_plan_create(nx, ny, nz, prec, ttype, layout, flags=0, check=True):
+    """Returns (status, plan handle or None)."""
+    h = ctypes.c_void_p()
+    tt = None if ttype is None else (ctypes.c_int * 3)(*ttype)
+    st = load().p3_plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(prec), tt, int(layout),
+                               int(flags))
+    if check:
+        _check(st, "p3_plan_create")
+    return st, (h.value if st == P3_OK else None)
+
+
+def p3_plan_destroy(plan):
+    return load().p3_plan_destroy(plan)
+
+
+def p3_ftran_r2c(plan, in_ptr, out_ptr, ws_ptr, stream, check=True):
+    st = load().p3_ftran_r2c(plan, in_ptr, out_ptr, ws_ptr, stream)
+    if check:
+        _check(st, "p3_ftran_r2c")
+    return st
+
+
+def p3_btran_c2r(plan, in_ptr, out_ptr, ws_ptr, stream, check=True):
+    st = load().p3_btran_c2r(plan, in_ptr, out_ptr, ws_ptr, stream)
+    if check:
+        _check(st, "p3_btran_c2r")
+    return st
+
+
+def p3_plan_get_dims(plan):
+    a, b = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+    _check(load().p3_plan_get_dims(plan, a, b), "p3_plan_get_dims")
+    return tuple(a), tuple(b)
+
+
+def p3_plan_workspace_bytes(plan) -> int:
+    v = ctypes.c_size_t()
+    _check(load().p3_plan_workspace_bytes(plan, ctypes.byref(v)), "p3_plan_workspace_bytes")
+    return v.value
+
+
+def p3_plan_scale(plan) -> float:
+    v = ctypes.c_double()
+    _check(load().p3_plan_scale(plan, ctypes.byref(v)), "p3_plan_scale")
+    return v.value
+
+
+def p3_plan_set_stage_events(plan, events):
+    if events is None:
+        _check(load().p3_plan_set_stage_events(plan, None, 0), "p3_plan_set_stage_events")
+        return
+    arr = (ctypes.c_void_p * len(events))(*events)
+    _check(load().p3_plan_set_stage_events(plan, arr, len(events)), "p3_plan_set_stage_events")
+
+
+def p3_plan_describe(plan) -> str:
+    buf = ctypes.create_string_buffer(1 << 14)
+    _check(load().p3_plan_describe(plan, buf, len(buf)), "p3_plan_describe")
+    return buf.value.decode()
+
+
+def p3_plan_launches(plan, direction: int) -> int:
+    v = ctypes.c_int()
+    _check(load().p3_plan_launches(plan, int(direction), ctypes.byref(v)), "p3_plan_launches")
+    return v.value
+
+
+# ---------------------------------------------------------------------------
+# torch-facing wrapper
+# ---------------------------------------------------------------------------
+
+_TT = {"fft": P3_FFT, "cheb": P3_CHEB, "empty": P3_EMPTY}
+_LAYOUT = {"zyx": P3_LAYOUT_ZYX, "xyz": P3_LAYOUT_XYZ}
+
+
+class Plan:
+    """A plan for an (nx, ny, nz) grid.  Real arrays are torch tensors of shape
+    (nz, ny, nx); complex arrays (nz, ny, H) for layout 'xyz' or (H, ny, nz)
+    for 'zyx', H = nx // 2 + 1."""
+
+    def __init__(self, nx, ny, nz, precision="f32", ttypes=("fft", "fft", "fft"), layout="zyx", device=None):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.H = self.nx // 2 + 1
+        self.precision = precision
+        self.ttypes = tuple(ttypes)
+        self.layout = layout
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            _, self.handle = p3_plan_create(self.nx, self.ny, self.nz, P3_F32 if precision == "f32" else P3_F64,
+                                            [_TT[t] for t in self.ttypes], _LAYOUT[layout])
+        self.real_dtype = torch.float32 if precision == "f32" else torch.float64
+        self.complex_dtype = torch.complex64 if precision == "f32" else torch.complex128
+        self.ws_bytes = p3_plan_workspace_bytes(self.handle)
+        self.scale = p3_plan_scale(self.handle)
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            p3_plan_destroy(h)
+            self.handle = None
+
+    @property
+    def real_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def complex_shape(self):
+        return (self.nz, self.ny, self.H) if self.layout == "xyz" else (self.H, self.ny, self.nz)
+
+    def empty_real(self):
+        return self.torch.empty(self.real_shape, dtype=self.real_dtype, device=self.device)
+
+    def empty_complex(self):
+        return self.torch.empty(self.complex_shape, dtype=self.complex_dtype, device=self.device)
+
+    def workspace(self):
+        if self.ws_bytes == 0:
+            return None
+        if self._ws is None:
+            self._ws = self.torch.empty(self.ws_bytes, dtype=self.torch.uint8, device=self.device)
+        return self._ws
+
+    def describe(self) -> str:
+        return p3_plan_describe(self.handle)
+
+    def launches(self, direction: int) -> int:
+        return p3_plan_launches(self.handle, direction)
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _check_tensor(self, t, shape, dtype, what):
+        if t.device != self.device or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor of shape %s on %s" % (what, dtype, shape, self.device))
+
+    def forward(self, x, out=None, ws=None, stream=None):
+        self._check_tensor(x, self.real_shape, self.real_dtype, "input")
+        out = self.empty_complex() if out is None else out
+        self._check_tensor(out, self.complex_shape, self.complex_dtype, "output")
+        ws = self.workspace() if ws is None else ws
+        p3_ftran_r2c(self.handle, x.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
+                     self._stream(stream))
+        return out
+
+    def backward(self, X, out=None, ws=None, stream=None):
+        self._check_tensor(X, self.complex_shape, self.complex_dtype, "input")
+        out = self.empty_real() if out is None else out
+        self._check_tensor(out, self.real_shape, self.real_dtype, "output")
+        ws = self.workspace() if ws is None else ws
+        p3_btran_c2r(self.handle, X.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
+                     self._stream(stream))
+        return out

@@ -1,0 +1,53 @@
+"""Shared helpers for the GPU parity tests (GPU path vs the FP64 oracle)."""
+import numpy as np
+
+import oracle as O
+from paper_1905_02803_gb300 import inputs
+
+TOL = {"f32": 2e-6, "f64": 1e-13}
+TT = {"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY}
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.complex128 if np.iscomplexobj(got) or np.iscomplexobj(ref) else np.float64)
+    ref = np.asarray(ref)
+    n = np.linalg.norm(ref.ravel())
+    d = np.linalg.norm((got - ref).ravel())
+    return d / n if n > 0 else d
+
+
+def random_complex(shape, seed):
+    n = int(np.prod(shape))
+    return (inputs.normal(seed, 60, n) + 1j * inputs.normal(seed, 62, n)).reshape(shape)
+
+
+def check_case(nx, ny, nz, prec="f64", ttypes=("fft", "fft", "fft"), layout="zyx", field=None, seed=0,
+               check_inverse=True):
+    """Forward of a real field and inverse of a random (non-Hermitian) complex
+    array, each compared element by element with the oracle; returns errors."""
+    import torch
+    from paper_1905_02803_gb300.p3dfft import Plan
+
+    plan = Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout)
+    if field is None:
+        field = inputs.uniform_field((nz, ny, nx), seed)
+    x = torch.from_numpy(np.ascontiguousarray(field)).to(device="cuda", dtype=plan.real_dtype)
+    X = plan.forward(x)
+    xin = x.double().cpu().numpy()  # the exact values the GPU saw
+    tt = tuple(TT[t] for t in ttypes)
+    ref = O.forward(xin, tt)
+    if layout == "zyx":
+        ref = O.to_zyx(ref)
+    torch.cuda.synchronize()
+    err_f = rel_l2(X.cpu().numpy(), ref)
+    err_b = None
+    if check_inverse:
+        G = random_complex((nz, ny, nx // 2 + 1), seed + 1)
+        Gd = torch.from_numpy(O.to_zyx(G) if layout == "zyx" else G).to(device="cuda", dtype=plan.complex_dtype)
+        g = plan.backward(Gd)
+        Gin = Gd.cpu().numpy().astype(np.complex128)
+        Gin = O.from_zyx(Gin) if layout == "zyx" else Gin
+        refb = O.backward(Gin, nx, tt)
+        torch.cuda.synchronize()
+        err_b = rel_l2(g.cpu().numpy(), refb)
+    return err_f, err_b, plan

@@ -1,0 +1,121 @@
+"""GPU path (through the C ABI) vs the FP64 CPU oracle, element by element.
+
+Tolerances: relative L2 <= 1e-13 for FP64 and <= 2e-6 for FP32.  Sizes span
+several CTA tiles with ragged tails, odd X lengths (no Nyquist bin), mixed
+radices 2/3/5/7, Bluestein lengths, degenerate extents of 1 and 2, the
+Chebyshev and empty third-dimension transforms, and both Z-pencil layouts.
+"""
+import numpy as np
+import pytest
+
+from paper_1905_02803_gb300 import inputs
+
+from _gpu_helpers import TOL, check_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_config1_32cubed_fp64_plane_wave(layout):
+    """32^3 FP64: U[-1,1) field plus sin(2 pi 3 x/32), and the plane wave alone."""
+    total, rnd, wave = inputs.config1_field(32, seed=0)
+    for field in (total, wave, rnd):
+        ef, eb, _ = check_case(32, 32, 32, "f64", layout=layout, field=field)
+        assert ef <= TOL["f64"] and eb <= TOL["f64"], (ef, eb)
+
+
+def test_plane_wave_single_bin_on_gpu():
+    import torch
+    from paper_1905_02803_gb300.p3dfft import Plan
+    plan = Plan(32, 32, 32, precision="f64", layout="xyz")
+    x = torch.from_numpy(inputs.plane_wave_sin((32, 32, 32), 3)).cuda()
+    X = plan.forward(x).cpu().numpy()
+    N = 32 ** 3
+    assert abs(X[0, 0, 3] - (-0.5j * N)) < 1e-9
+    X[0, 0, 3] = 0
+    assert np.abs(X).max() < 1e-10
+
+
+SHAPES = [
+    (64, 48, 40), (30, 20, 12), (7, 9, 15), (1, 1, 1), (2, 3, 5), (1, 7, 4), (9, 1, 1), (4, 1, 6),
+    (96, 7, 5), (49, 75, 343 // 7), (210, 6, 10), (16, 256, 8), (8, 8, 1024), (2048, 2, 2),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_fft3_parity(shape, prec, layout):
+    nx, ny, nz = shape
+    ef, eb, _ = check_case(nx, ny, nz, prec, layout=layout, seed=nx + ny + nz)
+    assert ef <= TOL[prec] and eb <= TOL[prec], (ef, eb)
+
+
+@pytest.mark.parametrize("shape", [(11, 13, 97), (22, 26, 14), (34, 17, 19), (12, 1, 23)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bluestein_lengths(shape, prec):
+    nx, ny, nz = shape
+    for layout in ("zyx", "xyz"):
+        ef, eb, plan = check_case(nx, ny, nz, prec, layout=layout, seed=3)
+        assert "bluestein" in plan.describe()
+        assert ef <= TOL[prec] and eb <= TOL[prec], (layout, ef, eb)
+
+
+@pytest.mark.parametrize("ttypes", [("fft", "fft", "cheb"), ("fft", "empty", "cheb"), ("fft", "empty", "empty"),
+                                    ("fft", "fft", "empty"), ("fft", "empty", "fft")])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_transform_types(ttypes, layout, prec):
+    for shape in ((20, 12, 17), (9, 5, 2), (16, 6, 33), (6, 4, 12)):
+        nx, ny, nz = shape
+        ef, eb, _ = check_case(nx, ny, nz, prec, ttypes=ttypes, layout=layout, seed=nz)
+        assert ef <= TOL[prec] and eb <= TOL[prec], (shape, ef, eb)
+
+
+def test_config4_channel_480x360x257_fp64():
+    """Uneven channel-flow grid: FFT in X and Y, Chebyshev (DCT-I) in Z."""
+    nx, ny, nz = 480, 360, 257
+    f = inputs.channel_field(nx, ny, nz, seed=0)
+    ef, eb, _ = check_case(nx, ny, nz, "f64", ttypes=("fft", "fft", "cheb"), layout="zyx", field=f)
+    assert ef <= TOL["f64"] and eb <= TOL["f64"], (ef, eb)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_turbulence_field_128(prec):
+    f = inputs.turbulence_field((96, 128, 128), seed=2)
+    ef, eb, _ = check_case(128, 128, 96, prec, field=f)
+    assert ef <= TOL[prec] and eb <= TOL[prec], (ef, eb)
+
+
+def test_round_trip_and_inputs_untouched():
+    import torch
+    from paper_1905_02803_gb300.p3dfft import Plan
+    for layout in ("zyx", "xyz"):
+        plan = Plan(40, 30, 20, precision="f64", layout=layout)
+        x = torch.from_numpy(inputs.uniform_field((20, 30, 40), 5)).cuda()
+        x0 = x.clone()
+        X = plan.forward(x)
+        X0 = X.clone()
+        y = plan.backward(X)
+        torch.cuda.synchronize()
+        assert torch.equal(x, x0) and torch.equal(X, X0)
+        assert rel_l2(y.cpu().numpy() / plan.scale, x0.cpu().numpy()) < 1e-14
+
+
+def test_error_paths_on_device():
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    plan = P.Plan(16, 8, 8, precision="f32", layout="zyx")
+    x = plan.empty_real().normal_()
+    X = plan.empty_complex()
+    ws = plan.workspace()
+    h = plan.handle
+    s = None
+    assert P.p3_ftran_r2c(h, x.data_ptr(), X.data_ptr(), None, s, check=False) == P.P3_ERR_WORKSPACE
+    assert P.p3_ftran_r2c(h, x.data_ptr(), x.data_ptr(), ws.data_ptr(), s, check=False) == P.P3_ERR_UNSUPPORTED
+    assert P.p3_ftran_r2c(h, x.data_ptr() + 4, X.data_ptr(), ws.data_ptr(), s, check=False) == P.P3_ERR_INVALID
+    assert P.p3_ftran_r2c(h, x.data_ptr(), X.data_ptr(), x.data_ptr(), s, check=False) == P.P3_ERR_INVALID
+    assert P.p3_ftran_r2c(h, x.data_ptr(), X.data_ptr(), ws.data_ptr(), s, check=False) == P.P3_OK
+    assert P.p3_plan_get_dims(h) == ((16, 8, 8), (8, 8, 9))
+    assert plan.ws_bytes == 9 * 8 * 8 * 8
+    torch.cuda.synchronize()
