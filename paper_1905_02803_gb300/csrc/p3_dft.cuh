@@ -1,0 +1,218 @@
+// Complex helpers and forward DFT butterflies (exp(-2 pi i n m / R)) of
+// sizes 2, 3, 4, 5, 7, 8, 16 and 32 on registers, shared by the stage kernels.
+// The inverse-sign DFT is swp(DFT(swp(x))), so only the forward form exists.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace p3 {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { typedef float2 t; };
+template <> struct Cx<double> { typedef double2 t; };
+
+template <class C> __device__ __forceinline__ C mk(decltype(C().x) x, decltype(C().x) y)
+{
+    C r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <class C> __device__ __forceinline__ C add(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C sub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C mul(C a, C b)
+{
+    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class C> __device__ __forceinline__ C cnj(C a) { return mk<C>(a.x, -a.y); }
+// (re, im) -> (im, re): conj(i * conj(a)).  swp(DFT(swp(x))) is the
+// inverse-sign DFT, so one forward FFT code serves both directions.
+template <class C> __device__ __forceinline__ C swp(C a) { return mk<C>(a.y, a.x); }
+// -i * a
+template <class C> __device__ __forceinline__ C mmi(C a) { return mk<C>(a.y, -a.x); }
+template <class C, class T> __device__ __forceinline__ C scl(C a, T s) { return mk<C>(a.x * s, a.y * s); }
+// a * (cr + i ci) with constant parts
+template <class C, class T> __device__ __forceinline__ C rot(C a, T cr, T ci)
+{
+    return mk<C>(a.x * cr - a.y * ci, a.x * ci + a.y * cr);
+}
+
+template <class C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// Forward DFT butterflies of size R on v[0..R), exp(-2 pi i n m / R), in place.
+// ---------------------------------------------------------------------------
+template <class C, class T>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3)
+{
+    C s02 = add(a0, a2), d02 = sub(a0, a2), s13 = add(a1, a3), d13 = mmi(sub(a1, a3));
+    a0 = add(s02, s13);
+    a2 = sub(s02, s13);
+    a1 = add(d02, d13);
+    a3 = sub(d02, d13);
+}
+
+template <class C, class T, int R> struct Dft;
+
+template <class C, class T> struct Dft<C, T, 2> {
+    static __device__ __forceinline__ void run(C* v)
+    {
+        C a = v[0];
+        v[0] = add(a, v[1]);
+        v[1] = sub(a, v[1]);
+    }
+};
+
+template <class C, class T> struct Dft<C, T, 4> {
+    static __device__ __forceinline__ void run(C* v) { dft4<C, T>(v[0], v[1], v[2], v[3]); }
+};
+
+template <class C, class T> struct Dft<C, T, 8> {
+    static __device__ __forceinline__ void run(C* v)
+    {
+        const T h = (T)0.7071067811865476;  // sqrt(1/2)
+        C u0 = add(v[0], v[4]), u1 = add(v[1], v[5]), u2 = add(v[2], v[6]), u3 = add(v[3], v[7]);
+        C w0 = sub(v[0], v[4]), w1 = sub(v[1], v[5]), w2 = sub(v[2], v[6]), w3 = sub(v[3], v[7]);
+        w1 = mk<C>(h * (w1.x + w1.y), h * (w1.y - w1.x));   // * exp(-i pi/4)
+        w2 = mmi(w2);                                       // * exp(-i pi/2)
+        w3 = mk<C>(h * (w3.y - w3.x), -h * (w3.x + w3.y));  // * exp(-3i pi/4)
+        dft4<C, T>(u0, u1, u2, u3);
+        dft4<C, T>(w0, w1, w2, w3);
+        v[0] = u0; v[2] = u1; v[4] = u2; v[6] = u3;
+        v[1] = w0; v[3] = w1; v[5] = w2; v[7] = w3;
+    }
+};
+
+template <class C, class T> struct Dft<C, T, 16> {
+    // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle exp(-2 pi i n2 k1/16),
+    // DFT4 over n2; the result X[k1 + 4 k2] lands in slot 4 k1 + k2.
+    static __device__ __forceinline__ void run(C* v)
+    {
+        const T c1 = (T)0.9238795325112867, s1 = (T)0.3826834323650898, h = (T)0.7071067811865476;
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft4<C, T>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+        v[5] = rot(v[5], c1, -s1);    // n2=1,k1=1: W^1
+        v[9] = rot(v[9], h, -h);      // n2=1,k1=2: W^2
+        v[13] = rot(v[13], s1, -c1);  // n2=1,k1=3: W^3
+        v[6] = rot(v[6], h, -h);      // n2=2,k1=1: W^2
+        v[10] = mmi(v[10]);           // n2=2,k1=2: W^4
+        v[14] = rot(v[14], -h, -h);   // n2=2,k1=3: W^6
+        v[7] = rot(v[7], s1, -c1);    // n2=3,k1=1: W^3
+        v[11] = rot(v[11], -h, -h);   // n2=3,k1=2: W^6
+        v[15] = rot(v[15], -c1, s1);  // n2=3,k1=3: W^9
+        // A[n2][k1] sits at v[n2 + 4 k1]; DFT4 over n2 for each k1
+        C o[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+            dft4<C, T>(a0, a1, a2, a3);
+            o[k1] = a0; o[k1 + 4] = a1; o[k1 + 8] = a2; o[k1 + 12] = a3;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = o[i];
+    }
+};
+
+template <class C, class T> struct Dft<C, T, 3> {
+    static __device__ __forceinline__ void run(C* v)
+    {
+        const T s3 = (T)0.8660254037844386;  // sqrt(3)/2
+        C t = add(v[1], v[2]), d = sub(v[1], v[2]);
+        C m = mk<C>(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
+        v[0] = add(v[0], t);
+        v[1] = mk<C>(m.x + s3 * d.y, m.y - s3 * d.x);
+        v[2] = mk<C>(m.x - s3 * d.y, m.y + s3 * d.x);
+    }
+};
+
+// Odd prime R: pair a_j with a_{R-j}; cos / sin of 2 pi t / R by table.
+template <class C, class T, int R> struct DftOdd {
+    static __device__ __forceinline__ T cs(int t)
+    {
+        if (R == 5) {
+            const double c[5] = {1.0, 0.30901699437494745, -0.8090169943749473, -0.8090169943749473,
+                                 0.30901699437494745};
+            return (T)c[t];
+        } else {
+            const double c[7] = {1.0, 0.6234898018587336, -0.22252093395631434, -0.900968867902419,
+                                 -0.900968867902419, -0.22252093395631434, 0.6234898018587336};
+            return (T)c[t];
+        }
+    }
+    static __device__ __forceinline__ T sn(int t)
+    {
+        if (R == 5) {
+            const double s[5] = {0.0, 0.9510565162951535, 0.5877852522924732, -0.5877852522924732,
+                                 -0.9510565162951535};
+            return (T)s[t];
+        } else {
+            const double s[7] = {0.0, 0.7818314824680298, 0.9749279121818236, 0.43388373911755823,
+                                 -0.43388373911755823, -0.9749279121818236, -0.7818314824680298};
+            return (T)s[t];
+        }
+    }
+    static __device__ __forceinline__ void run(C* v)
+    {
+        constexpr int h = (R - 1) / 2;
+        C p[h], q[h];
+#pragma unroll
+        for (int j = 1; j <= h; ++j) {
+            p[j - 1] = add(v[j], v[R - j]);
+            q[j - 1] = sub(v[j], v[R - j]);
+        }
+        C a0 = v[0];
+        C y0 = a0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) y0 = add(y0, p[j]);
+#pragma unroll
+        for (int m = 1; m <= h; ++m) {
+            C re = a0, im = mk<C>((T)0, (T)0);
+#pragma unroll
+            for (int j = 1; j <= h; ++j) {
+                const T c = cs((j * m) % R), s = sn((j * m) % R);
+                re = mk<C>(re.x + c * p[j - 1].x, re.y + c * p[j - 1].y);
+                im = mk<C>(im.x + s * q[j - 1].x, im.y + s * q[j - 1].y);
+            }
+            v[m] = mk<C>(re.x + im.y, re.y - im.x);      // re - i im
+            v[R - m] = mk<C>(re.x - im.y, re.y + im.x);  // re + i im
+        }
+        v[0] = y0;
+    }
+};
+// 32 = 2 x 16 (decimation in frequency): u_k = a_k + a_{k+16},
+// w_k = (a_k - a_{k+16}) exp(-2 pi i k / 32); even bins DFT16(u), odd DFT16(w).
+template <class C, class T> struct Dft<C, T, 32> {
+    static __device__ __forceinline__ void run(C* v)
+    {
+        // cos(pi k / 16), k = 0..8; sin(pi k / 16) = cos(pi (8 - k) / 16)
+        const T c[9] = {(T)1.0, (T)0.9807852804032304, (T)0.9238795325112867, (T)0.8314696123025452,
+                        (T)0.7071067811865476, (T)0.5555702330196022, (T)0.3826834323650898,
+                        (T)0.19509032201612825, (T)0.0};
+        C u[16], w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            u[k] = add(v[k], v[k + 16]);
+            const C d = sub(v[k], v[k + 16]);
+            // angle pi k / 16: cos / sin from the first-octant table
+            const T ck = k <= 8 ? c[k] : -c[16 - k];
+            const T sk = k <= 8 ? c[8 - k] : c[k - 8];
+            w[k] = rot(d, ck, -sk);
+        }
+        Dft<C, T, 16>::run(u);
+        Dft<C, T, 16>::run(w);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[2 * k] = u[k];
+            v[2 * k + 1] = w[k];
+        }
+    }
+};
+
+template <class C, class T> struct Dft<C, T, 5> {
+    static __device__ __forceinline__ void run(C* v) { DftOdd<C, T, 5>::run(v); }
+};
+template <class C, class T> struct Dft<C, T, 7> {
+    static __device__ __forceinline__ void run(C* v) { DftOdd<C, T, 7>::run(v); }
+};
+
+}  // namespace p3

@@ -25,6 +25,16 @@ struct LineMap {
     long long per, gstride, lstride, es;
 };
 
+// Stage kernel families (StageArgs::kern).
+enum KernelKind : int {
+    KIND_GENERIC = 0,  // runtime mixed radix / Bluestein, any length
+    KIND_COL_DD = 1,   // power of two, strided lines, HBM -> regs -> HBM
+    KIND_COL_DS = 2,   // power of two, strided in, element-contiguous out (ZYX store)
+    KIND_COL_SD = 3,   // power of two, element-contiguous in (ZYX load), strided out
+    KIND_ROW_R2C = 4,  // power-of-two half length, X-stage real-to-complex
+    KIND_ROW_C2R = 5,  // power-of-two half length, X-stage complex-to-real
+};
+
 enum StageOp : int {
     OP_C2C = 0,       // complex line -> complex line
     OP_R2C_HALF = 1,  // even Nx: length Nx/2 complex FFT of (f[2j], f[2j+1]) + real split
@@ -66,6 +76,7 @@ struct StageArgs {
     const void* twm;   // exp(-2 pi i k / m), k < m
     size_t smem;       // dynamic shared memory bytes
     int threads;       // B * tpl
+    int kern;          // KernelKind
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.
@@ -73,5 +84,11 @@ cudaError_t launch_stage_f32(const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageArgs& a, cudaStream_t s);
 // One-time kernel attribute set-up for the current device (max dynamic smem).
 cudaError_t prepare_kernels();
+
+// Power-of-two specialised kernels (p3_pow2.cu): configure a stage for them
+// (returns false when none applies), set them up, launch one stage.
+bool pow2_configure(StageArgs& a, size_t csize);
+cudaError_t pow2_prepare();
+cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t s);
 
 }  // namespace p3

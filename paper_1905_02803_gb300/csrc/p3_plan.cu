@@ -275,6 +275,8 @@ void tile_setup(StageArgs& a, size_t csize)
     th = (th + 31) / 32 * 32;
     a.threads = th;
     a.smem = (size_t)len * (size_t)a.LDB * csize;
+    a.kern = p3::KIND_GENERIC;
+    p3::pow2_configure(a, csize);
 }
 
 LineMap rows(long long nlines, long long pitch) { return LineMap{nlines > 0 ? nlines : 1, 0, pitch, 1}; }
@@ -289,6 +291,18 @@ const char* op_name(int op)
     case p3::OP_C2R_FULL: return "c2r_full";
     case p3::OP_DCT1: return "dct1";
     default: return "copy";
+    }
+}
+
+const char* kern_name(int k)
+{
+    switch (k) {
+    case p3::KIND_COL_DD: return "pow2_col";
+    case p3::KIND_COL_DS: return "pow2_col_zyx_store";
+    case p3::KIND_COL_SD: return "pow2_col_zyx_load";
+    case p3::KIND_ROW_R2C: return "pow2_row_r2c";
+    case p3::KIND_ROW_C2R: return "pow2_row_c2r";
+    default: return "generic";
     }
 }
 
@@ -534,9 +548,9 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             }
             if (rs.empty()) rs = "-";
             snprintf(line, sizeof(line),
-                     "%s %s op=%s nfft=%d%s radices=%s lines=%lld B=%d LDB=%d tpl=%d threads=%d smem=%zu "
-                     "bytes=%.0f\n",
-                     d == 0 ? "fwd" : "bwd", s.name, op_name(a.op), a.nfft,
+                     "%s %s kernel=%s op=%s nfft=%d%s radices=%s lines=%lld B=%d LDB=%d tpl=%d threads=%d "
+                     "smem=%zu bytes=%.0f\n",
+                     d == 0 ? "fwd" : "bwd", s.name, kern_name(a.kern), op_name(a.op), a.nfft,
                      a.blue ? (" bluestein_m=" + std::to_string(a.m)).c_str() : "", rs.c_str(), a.nlines, a.B,
                      a.LDB, a.tpl, a.threads, a.smem, s.bytes);
             P->desc += line;

@@ -119,3 +119,26 @@ def test_error_paths_on_device():
     assert P.p3_plan_get_dims(h) == ((16, 8, 8), (8, 8, 9))
     assert plan.ws_bytes == 9 * 8 * 8 * 8
     torch.cuda.synchronize()
+
+
+POW2_SHAPES = [(128, 64, 256), (256, 128, 64), (1024, 4, 6), (4096, 2, 3), (8192, 1, 2), (6, 4096, 2),
+               (10, 3, 2048), (130, 64, 64), (64, 2, 4096)]
+
+
+@pytest.mark.parametrize("shape", POW2_SHAPES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_pow2_kernels_parity(shape, prec, layout):
+    nx, ny, nz = shape
+    ef, eb, plan = check_case(nx, ny, nz, prec, layout=layout, seed=7)
+    assert "pow2_" in plan.describe()
+    assert ef <= TOL[prec] and eb <= TOL[prec], (ef, eb)
+
+
+@pytest.mark.parametrize("nz", [65, 129, 257, 1025])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_pow2_chebyshev(nz, layout):
+    for prec in ("f64", "f32"):
+        ef, eb, plan = check_case(12, 6, nz, prec, ttypes=("fft", "fft", "cheb"), layout=layout, seed=nz)
+        assert "pow2_col" in plan.describe()
+        assert ef <= TOL[prec] and eb <= TOL[prec], (prec, ef, eb)
