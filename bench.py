@@ -209,10 +209,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--grid", type=int, default=1024, help="cubic grid edge (1024 is the benchmark workload)")
+    ap.add_argument("--grid", default="1024",
+                    help="grid edge N, or NX,NY,NZ (1024 is the benchmark workload; others are for profiling)")
     args = ap.parse_args()
     global NX, NY, NZ
-    NX = NY = NZ = args.grid
+    g = [int(v) for v in str(args.grid).split(",")]
+    NX, NY, NZ = (g * 3)[:3] if len(g) == 1 else g
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

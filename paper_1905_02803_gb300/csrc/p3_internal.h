@@ -77,6 +77,13 @@ struct StageArgs {
     size_t smem;       // dynamic shared memory bytes
     int threads;       // B * tpl
     int kern;          // KernelKind
+    // Optional group-major tiling (power-of-two column kernels): lines form
+    // gcount groups of glen adjacent lines (L = g * glen + x); tile i takes
+    // group i % gcount and lines x = (i / gcount) * B + l, so CTAs running
+    // side by side work on different groups.  gcount = 0: tile i takes lines
+    // i * B + l.
+    long long gcount;
+    int glen;
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.

@@ -27,6 +27,10 @@
 #include "../../include/p3dfft_gb300.h"
 #include "p3_internal.h"
 
+#ifndef P3_Z_GROUP_MAJOR
+#define P3_Z_GROUP_MAJOR 0
+#endif
+
 using p3::LineMap;
 using p3::StageArgs;
 
@@ -415,6 +419,15 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.npass = 0;
         }
         tile_setup(a, P->csize);
+        a.gcount = 0;
+        a.glen = 0;
+        if (name[0] == 'z' && a.kern >= p3::KIND_COL_DD && a.kern <= p3::KIND_COL_SD && P3_Z_GROUP_MAJOR) {
+            // Z lines (x, y): CTAs side by side take different y rows, so the
+            // plane-strided accesses of concurrent tiles spread over memory
+            // channels instead of repeating the same plane-pitch offsets.
+            a.gcount = NY;
+            a.glen = (int)H;
+        }
         Stage s;
         s.a = a; s.src = src; s.dst = dst; s.name = name; s.bytes = bytes;
         P->st[dir].push_back(s);

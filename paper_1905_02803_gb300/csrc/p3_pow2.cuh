@@ -1,0 +1,455 @@
+// Specialised stage kernels for power-of-two line lengths (64 .. 4096): the
+// hot path of the 3D transform (Sect. 2, Sect. 3.3 of the P3DFFT paper) with
+// every pass, radix, index and direction known at compile time.
+//
+// Column kernels (Y and Z stages: lines whose neighbours are adjacent in
+// memory, elements far apart).  Lanes walk B adjacent lines, so each global
+// access of a line element is one coalesced B-wide run.  Each thread keeps E
+// values of one line in registers (E = 16 or 32, one radix-E butterfly per
+// pass); the first Stockham pass loads its butterfly inputs straight from
+// HBM, the last pass stores straight to HBM, and shared memory is touched only
+// for the exchanges between passes.  The Z stage that writes (or, inverse,
+// reads) the STRIDE1 ZYX layout (Table 1) routes that side through shared
+// memory with lanes along the line, 128 contiguous bytes per line per warp:
+// the fused re-orientation that replaces the paper's COLUMN all-to-all and
+// local transpose.
+//
+// Row kernels (X stage: contiguous lines).  Lanes walk the butterflies of one
+// row; the real-to-complex split of an even-length line (a length Nx/2 complex
+// FFT of (f[2j], f[2j+1]) plus the post-twiddle) and its inverse pre-twiddle
+// are fused into the first / last pass.
+//
+// Shared-memory slots.  Columns: element e of tile line l lives at
+// cpad(e) * B + (l ^ sw(e)) with cpad(e) = e + e/16 + e/32; the padding keeps
+// the stride-E writes of the first pass and the unit-stride reads of later
+// passes in distinct banks for the two line groups of a half-warp, and the
+// XOR swizzle (ZYX kernels only) does the same for the element-contiguous
+// phases.  Rows: row l at l * RP, element e at e + e/E.  Offsets that are
+// multiples of 32 split off cpad exactly, so most slot addresses are a
+// per-thread base plus an immediate.
+#pragma once
+
+#include "p3_dft.cuh"
+#include "p3_internal.h"
+
+namespace p3 {
+namespace pw {
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+// Radix plan of an N-point line with E values per thread: radix E while it
+// divides, then one remainder pass.
+template <int N, int E> struct P2 {
+    static constexpr int LOGN = ilog2(N), LOGE = ilog2(E);
+    static constexpr int NFULL = LOGN / LOGE;
+    static constexpr int REM = 1 << (LOGN - NFULL * LOGE);
+    static constexpr int NPASS = NFULL + (REM > 1 ? 1 : 0);
+    static constexpr int TPL = N / E;
+    __host__ __device__ static constexpr int radix(int p) { return p < NFULL ? E : REM; }
+    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+};
+
+__device__ __forceinline__ int cpad(int e) { return e + (e >> 4) + (e >> 5); }
+__host__ __device__ constexpr int cpad_c(int e) { return e + (e >> 4) + (e >> 5); }
+
+// Pass P: butterfly b of thread t is j = t + b * TPL; it reads j + r N/R and
+// writes (j / NS) NS R + j % NS + r NS.  Each index is split into a per-thread
+// part u(t) and a compile-time part K(b, r) with alignment UA of u.
+template <int N, int E, int P> struct PassIdx {
+    typedef P2<N, E> PL;
+    static constexpr int R = PL::radix(P), NS = PL::ns(P), BM = E / R, TPL = PL::TPL;
+    static __device__ __forceinline__ int in_u(int t) { return t; }
+    __host__ __device__ static constexpr int in_K(int b, int r) { return b * TPL + r * (N / R); }
+    static constexpr int IN_UA = 1;
+    // NS <= TPL: j % NS = t % NS and j / NS = t / NS + b TPL / NS; otherwise j < NS
+    static constexpr bool OUT_SPLIT = NS <= TPL;
+    static __device__ __forceinline__ int out_u(int t) { return OUT_SPLIT ? (t / NS) * NS * R + (t % NS) : t; }
+    __host__ __device__ static constexpr int out_K(int b, int r) { return OUT_SPLIT ? b * TPL * R + r * NS : b * TPL + r * NS; }
+    static constexpr int OUT_UA = (NS == 1) ? R : 1;
+};
+
+template <class T, int B, bool SWZ> struct ColSlot {
+    static constexpr int SH = (sizeof(T) == 8 && B >= 8) ? 0 : 1;
+    static constexpr int SWM = B << SH;  // swizzle period in elements
+    static __device__ __forceinline__ int at(int e, int l)
+    {
+        return SWZ ? cpad(e) * B + (l ^ ((e >> SH) & (B - 1))) : cpad(e) * B + l;
+    }
+    // slot of element u + K (K a constant after unrolling, u aligned to UA):
+    // per-thread base plus immediate whenever that is exact
+    static __device__ __forceinline__ int at_k(int u, int l, int K, int UA)
+    {
+        const bool padsplit = (K % 32) == 0 || (UA % 32) == 0;
+        if (!padsplit) return at(u + K, l);
+        if (!SWZ || (K % SWM) == 0) return at(u, l) + cpad_c(K) * B;
+        if ((UA % SWM) == 0) return cpad(u) * B + cpad_c(K) * B + (l ^ ((K >> SH) & (B - 1)));
+        return at(u + K, l);
+    }
+};
+
+template <class T> struct CxT;
+template <> struct CxT<float> { typedef float2 t; };
+template <> struct CxT<double> { typedef double2 t; };
+
+template <int NT, int CSIZE, int E> struct MinBlocks {
+    static constexpr int value =
+        CSIZE == 8 ? (E == 32 ? (NT >= 512 ? 1 : 2) : (NT >= 512 ? 2 : 3)) : (NT >= 512 ? 1 : 2);
+};
+
+__device__ __forceinline__ long long lbase(const LineMap& m, long long L)
+{
+    return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
+}
+
+// Line of tile lane l (see StageArgs::gcount); returns false past the end.
+__device__ __forceinline__ bool tile_line(const StageArgs& a, int B, int l, long long* L)
+{
+    if (a.gcount > 0) {
+        const long long g = blockIdx.x % a.gcount;
+        const int x = (int)(blockIdx.x / a.gcount) * B + l;
+        *L = g * a.glen + x;
+        return x < a.glen;
+    }
+    *L = (long long)blockIdx.x * B + l;
+    return *L < a.nlines;
+}
+
+// twiddle multiply of pass P for butterfly b (tw[k] = exp(-2 pi i k / twn),
+// stride ts per FFT index), then DFT_R in registers
+template <class C, class T, int N, int E, int P>
+__device__ __forceinline__ void pass_compute(C (&v)[E], int t, const C* tw, int ts)
+{
+    typedef PassIdx<N, E, P> PI;
+    constexpr int R = PI::R, NS = PI::NS;
+#pragma unroll
+    for (int b = 0; b < PI::BM; ++b) {
+        if constexpr (NS > 1) {
+            const int j = t + b * PI::TPL;
+            const int step = (j % NS) * (N / (NS * R)) * ts;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b * R + r] = mul(v[b * R + r], ldg(tw + step * r));
+        }
+        Dft<C, T, R>::run(&v[b * R]);
+    }
+}
+
+// Exchanges and passes 1 .. NP-1 through a column tile in shared memory.
+template <class C, class T, int N, int E, int B, bool SWZ, int P, int NP> struct ColRest {
+    static __device__ __forceinline__ void run(C (&v)[E], C* s, int l, int t, const C* tw)
+    {
+        typedef PassIdx<N, E, P - 1> Pr;
+        typedef PassIdx<N, E, P> Cu;
+        typedef ColSlot<T, B, SWZ> S;
+        __syncthreads();
+        {
+            const int u = Pr::out_u(t);
+#pragma unroll
+            for (int b = 0; b < Pr::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < Pr::R; ++r)
+                    s[S::at_k(u, l, Pr::out_K(b, r), Pr::OUT_UA)] = v[b * Pr::R + r];
+        }
+        __syncthreads();
+        {
+            const int u = Cu::in_u(t);
+#pragma unroll
+            for (int b = 0; b < Cu::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < Cu::R; ++r) v[b * Cu::R + r] = s[S::at_k(u, l, Cu::in_K(b, r), 1)];
+        }
+        pass_compute<C, T, N, E, P>(v, t, tw, 1);
+        ColRest<C, T, N, E, B, SWZ, P + 1, NP>::run(v, s, l, t, tw);
+    }
+};
+template <class C, class T, int N, int E, int B, bool SWZ, int NP> struct ColRest<C, T, N, E, B, SWZ, NP, NP> {
+    static __device__ __forceinline__ void run(C (&)[E], C*, int, int, const C*) {}
+};
+
+template <class T, int N> __host__ __device__ constexpr int col_smem_slots() { return cpad_c(N - 1) + 1; }
+
+// Element-contiguous phases of a column tile (the ZYX side): EL lanes per
+// line, VEC elements per lane (16 bytes), 128 contiguous bytes of each of
+// 32/EL lines per warp instruction.
+template <class T, int N, int E, int B> struct EF {
+    static constexpr int TPL = N / E, NT = B * TPL;
+    static constexpr int VEC = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int ELD = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int EL = ELD < TPL ? ELD : TPL;
+    static constexpr int STEP = NT / B;
+    static __device__ __forceinline__ int line(int tid) { return (tid / EL) % B; }
+    static __device__ __forceinline__ int chunk0(int tid) { return (tid % EL) + EL * (tid / (EL * B)); }
+};
+
+template <class T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 t; };
+
+// MODE 0: HBM -> regs ... regs -> HBM (both sides line-adjacent)
+// MODE 1: HBM -> regs ... smem -> HBM with lanes along elements (ZYX store)
+// MODE 2: HBM (lanes along elements) -> smem -> regs ... regs -> HBM (ZYX load)
+// INV: inverse sign (swp on load and store); DCT: Chebyshev even extension.
+template <typename T, int N, int E, int B, int MODE, bool INV, bool DCT>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    col_kernel(const __grid_constant__ StageArgs a)
+{
+    typedef typename CxT<T>::t C;
+    typedef P2<N, E> PL;
+    constexpr int NP = PL::NPASS;
+    constexpr bool SWZ = MODE != 0;
+    typedef ColSlot<T, B, SWZ> S;
+    typedef EF<T, N, E, B> Ef;
+    constexpr int M = N / 2;  // Chebyshev lines hold M + 1 points
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, l = tid % B, t = tid / B;
+    long long L;
+    const bool valid = tile_line(a, B, l, &L);
+    const C zero = mk<C>((T)0, (T)0);
+    const C* tw = static_cast<const C*>(a.tw);
+    C v[E];
+    typedef PassIdx<N, E, 0> P0;
+
+    if constexpr (MODE != 2) {
+        const C* src = static_cast<const C*>(a.src) + (valid ? lbase(a.in, L) : 0);
+        const long long es = a.in.es;
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) {
+                const int K = P0::in_K(b, r);
+                const int e = t + K;
+                // even extension of a Chebyshev line: element e > M reads N - e
+                const long long off = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
+                C x = valid ? src[off] : zero;
+                v[b * P0::R + r] = INV ? swp(x) : x;
+            }
+    } else {
+        const int le = Ef::line(tid);
+        long long Le;
+        const bool ve = tile_line(a, B, le, &Le);
+        const C* src = static_cast<const C*>(a.src) + (ve ? lbase(a.in, Le) : 0);
+        if constexpr (DCT || Ef::VEC == 1) {
+            for (int c = Ef::chunk0(tid); c < N; c += Ef::STEP) {
+                const int ee = DCT ? (c <= M ? c : N - c) : c;
+                C x = ve ? src[ee] : zero;
+                s[S::at(c, le)] = INV ? swp(x) : x;
+            }
+        } else {
+            typedef typename Vec4<T>::t V;
+            const V* src4 = reinterpret_cast<const V*>(src);
+            for (int c = Ef::chunk0(tid); c < N / 2; c += Ef::STEP) {
+                V q = ve ? src4[c] : V{(T)0, (T)0, (T)0, (T)0};
+                C x0 = mk<C>(q.x, q.y), x1 = mk<C>(q.z, q.w);
+                s[S::at(2 * c, le)] = INV ? swp(x0) : x0;
+                s[S::at(2 * c + 1, le)] = INV ? swp(x1) : x1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) v[b * P0::R + r] = s[S::at(t + P0::in_K(b, r), l)];
+    }
+    pass_compute<C, T, N, E, 0>(v, t, tw, 1);
+    ColRest<C, T, N, E, B, SWZ, 1, NP>::run(v, s, l, t, tw);
+
+    typedef PassIdx<N, E, NP - 1> PLast;
+    if constexpr (MODE != 1) {
+        if (valid) {
+            C* dst = static_cast<C*>(a.dst) + lbase(a.out, L);
+            const long long es = a.out.es;
+            const int u = PLast::out_u(t);
+#pragma unroll
+            for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < PLast::R; ++r) {
+                    const int e = u + PLast::out_K(b, r);
+                    const C x = v[b * PLast::R + r];
+                    if (!DCT || e <= M) dst[(long long)e * es] = INV ? swp(x) : x;
+                }
+        }
+    } else {
+        __syncthreads();
+        {
+            const int u = PLast::out_u(t);
+#pragma unroll
+            for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < PLast::R; ++r)
+                    s[S::at_k(u, l, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
+        }
+        __syncthreads();
+        const int le = Ef::line(tid);
+        long long Le;
+        if (tile_line(a, B, le, &Le)) {
+            C* dst = static_cast<C*>(a.dst) + lbase(a.out, Le);
+            if constexpr (DCT || Ef::VEC == 1) {
+                for (int c = Ef::chunk0(tid); c < (DCT ? M + 1 : N); c += Ef::STEP) {
+                    const C x = s[S::at(c, le)];
+                    dst[c] = INV ? swp(x) : x;
+                }
+            } else {
+                typedef typename Vec4<T>::t V;
+                V* dst4 = reinterpret_cast<V*>(dst);
+                for (int c = Ef::chunk0(tid); c < N / 2; c += Ef::STEP) {
+                    C x0 = s[S::at(2 * c, le)], x1 = s[S::at(2 * c + 1, le)];
+                    if (INV) {
+                        x0 = swp(x0);
+                        x1 = swp(x1);
+                    }
+                    dst4[c] = V{x0.x, x0.y, x1.x, x1.y};
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row kernels: X stage, Nx = 2N real points per row, H = N + 1 bins.
+// OPR 0: r2c (forward), OPR 1: c2r (inverse).
+// ---------------------------------------------------------------------------
+template <int N, int E> struct RowSlot {
+    static constexpr int RP = N + N / E + 1;  // odd pitch between rows
+    static __device__ __forceinline__ int at(int e) { return e + e / E; }
+    static __device__ __forceinline__ int at_k(int u, int K, int UA)
+    {
+        if ((K % E) == 0 || (UA % E) == 0) return at(u) + K + K / E;
+        return at(u + K);
+    }
+};
+
+template <class C, class T, int N, int E, int P, int NP> struct RowRest {
+    static __device__ __forceinline__ void run(C (&v)[E], C* s, int t, const C* tw)
+    {
+        typedef PassIdx<N, E, P - 1> Pr;
+        typedef PassIdx<N, E, P> Cu;
+        typedef RowSlot<N, E> S;
+        __syncthreads();
+        {
+            const int u = Pr::out_u(t);
+#pragma unroll
+            for (int b = 0; b < Pr::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < Pr::R; ++r)
+                    s[S::at_k(u, Pr::out_K(b, r), Pr::OUT_UA)] = v[b * Pr::R + r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < Cu::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < Cu::R; ++r) v[b * Cu::R + r] = s[S::at_k(t, Cu::in_K(b, r), 1)];
+        pass_compute<C, T, N, E, P>(v, t, tw, 2);
+        RowRest<C, T, N, E, P + 1, NP>::run(v, s, t, tw);
+    }
+};
+template <class C, class T, int N, int E, int NP> struct RowRest<C, T, N, E, NP, NP> {
+    static __device__ __forceinline__ void run(C (&)[E], C*, int, const C*) {}
+};
+
+template <typename T, int N, int E, int B, int OPR>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    row_kernel(const __grid_constant__ StageArgs a)
+{
+    typedef typename CxT<T>::t C;
+    typedef P2<N, E> PL;
+    constexpr int TPL = PL::TPL, NP = PL::NPASS;
+    typedef RowSlot<N, E> S;
+    constexpr int H = N + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
+    const long long L = (long long)blockIdx.x * B + l;
+    const bool valid = L < a.nlines;
+    const C zero = mk<C>((T)0, (T)0);
+    const C* tw2 = static_cast<const C*>(a.tw2);  // exp(-2 pi i k / 2N), k < 2N
+    C* srow = s + l * S::RP;
+    C v[E];
+    typedef PassIdx<N, E, 0> P0;
+    typedef PassIdx<N, E, NP - 1> PLast;
+
+    if constexpr (OPR == 0) {
+        // z[j] = f[2j] + i f[2j+1]
+        const C* src = reinterpret_cast<const C*>(static_cast<const T*>(a.src) + (valid ? L * (2LL * N) : 0));
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) v[b * P0::R + r] = valid ? src[t + P0::in_K(b, r)] : zero;
+    } else {
+        // Z[k] = (F[k] + conj F[N-k]) + i (F[k] - conj F[N-k]) exp(+2 pi i k / 2N),
+        // imaginary parts of F[0] and F[N] dropped; inverse via swp
+        const C* src = static_cast<const C*>(a.src) + (valid ? L * (long long)H : 0);
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) {
+                const int k = t + P0::in_K(b, r);
+                C A = valid ? src[k] : zero;
+                C Bc = valid ? cnj(src[N - k]) : zero;
+                if (k == 0) {
+                    A.y = (T)0;
+                    Bc.y = (T)0;
+                }
+                const C ze = add(A, Bc);
+                const C zo = mul(sub(A, Bc), cnj(ldg(tw2 + k)));
+                v[b * P0::R + r] = swp(mk<C>(ze.x - zo.y, ze.y + zo.x));
+            }
+    }
+    pass_compute<C, T, N, E, 0>(v, t, tw2, 2);
+    RowRest<C, T, N, E, 1, NP>::run(v, srow, t, tw2);
+
+    if constexpr (OPR == 0) {
+        __syncthreads();
+        {
+            const int u = PLast::out_u(t);
+#pragma unroll
+            for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < PLast::R; ++r)
+                    srow[S::at_k(u, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
+        }
+        __syncthreads();
+        if (valid) {
+            C* dst = static_cast<C*>(a.dst) + L * (long long)H;
+            for (int k = t; k <= N; k += TPL) {
+                const C zk = srow[S::at(k == N ? 0 : k)];
+                const C zm = cnj(srow[S::at(k == 0 ? 0 : N - k)]);
+                const C p = mul(ldg(tw2 + k), sub(zk, zm));
+                dst[k] = mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x));
+            }
+        }
+    } else {
+        if (valid) {
+            C* dst = reinterpret_cast<C*>(static_cast<T*>(a.dst) + L * (2LL * N));
+            const int u = PLast::out_u(t);
+#pragma unroll
+            for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+                for (int r = 0; r < PLast::R; ++r) dst[u + PLast::out_K(b, r)] = swp(v[b * PLast::R + r]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile shapes per precision and length
+// ---------------------------------------------------------------------------
+#ifndef P3_COL_E32
+#define P3_COL_E32 1
+#endif
+// E = 32 (two radix-32 passes for 1024 points) for the FP32 kernels whose
+// first pass reads HBM directly; the ZYX-load kernel keeps E = 16.
+template <typename T> __host__ __device__ constexpr int col_E(int N, int mode)
+{
+    return (sizeof(T) == 4 && P3_COL_E32 && mode != 2 && N >= 512 && N <= 2048) ? 32 : 16;
+}
+template <typename T> __host__ __device__ constexpr int col_B(int N)
+{
+    return sizeof(T) == 4 ? (N <= 64 ? 64 : N <= 128 ? 32 : N <= 256 ? 16 : N <= 2048 ? 8 : 4)
+                          : (N <= 64 ? 64 : N <= 128 ? 32 : N <= 256 ? 16 : N <= 512 ? 8 : N <= 2048 ? 4 : 2);
+}
+template <typename T> __host__ __device__ constexpr int row_E(int N) { return 16; }
+template <typename T> __host__ __device__ constexpr int row_B(int N)
+{
+    return N <= 64 ? 64 : N <= 128 ? 32 : N <= 256 ? 16 : N <= 512 ? 8 : N <= 1024 ? 4 : N <= 2048 ? 2 : 1;
+}
+
+}  // namespace pw
+}  // namespace p3
