@@ -150,6 +150,31 @@ p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len);
 /* Number of kernel launches one ftran (dir = 0) or btran (dir = 1) makes. */
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
 
+/*
+ * p3_ftran_r2c_noalloc -- the forward transform of p3_ftran_r2c, but with the
+ * workspace taken from a fixed device array built into the library instead
+ * of from the caller.  The paper has no counterpart: this exists for callers
+ * that must not allocate device memory when they run a transform (an
+ * application that hands out all device memory from its own pre-sized pool
+ * and forbids libraries to call cudaMalloc, or a latency-bound loop that
+ * cannot afford a cudaMalloc/cudaFree, which can synchronise the device).
+ * This call allocates nothing; the plan (created beforehand, which allocates
+ * its small tables once) and the input / output buffers are the caller's.
+ *   - The array holds P3_NOALLOC_SCRATCH_BYTES bytes per device, for as long
+ *     as the process runs, on every GPU that loads the library.  Plans whose
+ *     p3_plan_workspace_bytes() exceeds it get P3_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture begins.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (the transform overwrites every workspace element before reading it,
+ *     so nothing needs clearing).  Calls whose kernels overlap on the GPU --
+ *     on different streams, or from different threads -- race on it.
+ *   - Errors as p3_ftran_r2c, plus P3_ERR_UNSUPPORTED for the size limit.
+ */
+#define P3_NOALLOC_SCRATCH_BYTES (64u << 20)
+p3_status p3_ftran_r2c_noalloc(p3_plan plan, const void* in_real, void* out_cplx, void* stream);
+
 /* Static string for a status code; never NULL. */
 const char* p3_status_string(p3_status s);
 

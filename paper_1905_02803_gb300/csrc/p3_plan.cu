@@ -700,3 +700,11 @@ p3_status p3_plan_launches(p3_plan plan, int dir, int* launches)
 }
 
 }  // extern "C"
+
+namespace p3 {
+p3_status run_direction(p3_plan plan, int dir, const void* in, void* out, void* ws, void* stream)
+{
+    return run(plan, dir, in, out, ws, stream);
+}
+size_t plan_workspace(p3_plan plan) { return plan ? plan->ws_bytes : 0; }
+}  // namespace p3

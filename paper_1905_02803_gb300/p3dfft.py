@@ -19,7 +19,8 @@ P3_F32, P3_F64 = 0, 1
 P3_FFT, P3_CHEB, P3_EMPTY = 0, 1, 2
 P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
 
-EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_plan_get_dims",
+EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
+           "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
            "p3_plan_launches", "p3_status_string", "p3_version")
 
@@ -46,6 +47,7 @@ def load():
     lib.p3_plan_destroy.argtypes = [P]
     lib.p3_ftran_r2c.argtypes = [P, P, P, P, P]
     lib.p3_btran_c2r.argtypes = [P, P, P, P, P]
+    lib.p3_ftran_r2c_noalloc.argtypes = [P, P, P, P]
     lib.p3_plan_get_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.p3_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     lib.p3_plan_scale.argtypes = [P, ctypes.POINTER(D)]
@@ -101,6 +103,19 @@ def p3_btran_c2r(plan, in_ptr, out_ptr, ws_ptr, stream, check=True):
     st = load().p3_btran_c2r(plan, in_ptr, out_ptr, ws_ptr, stream)
     if check:
         _check(st, "p3_btran_c2r")
+    return st
+
+
+# Bytes of the library's built-in scratch array (include/p3dfft_gb300.h).
+P3_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def p3_ftran_r2c_noalloc(plan, in_ptr, out_ptr, stream, check=True):
+    """Forward transform whose workspace is the library's built-in device
+    array: for callers that must not allocate device memory at call time."""
+    st = load().p3_ftran_r2c_noalloc(plan, in_ptr, out_ptr, stream)
+    if check:
+        _check(st, "p3_ftran_r2c_noalloc")
     return st
 
 
