@@ -43,9 +43,10 @@ def _load():
     lib.p3o_c2c_lines.argtypes = [L, L, L, L, L, P, L, L, I, I]
     lib.p3o_dct1_lines.argtypes = [L, L, L, L, L, P, L, L, I]
     lib.p3o_forward.argtypes = [L, L, L, I, I, P, P, I]
+    lib.p3o_phase_sum_yz.argtypes = [L, L, L, P, I, L, L, L, P, P, I, P, I]
     lib.p3o_backward.argtypes = [L, L, L, I, I, P, P, I]
     for name in ("p3o_fft1d", "p3o_dct1", "p3o_x_r2c_rows", "p3o_x_c2r_rows",
-                 "p3o_c2c_lines", "p3o_dct1_lines", "p3o_forward", "p3o_backward"):
+                 "p3o_c2c_lines", "p3o_dct1_lines", "p3o_forward", "p3o_backward", "p3o_phase_sum_yz"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -143,3 +144,45 @@ def c2c_lines(n, per, gstride, lstride, es, data, l0, l1, sign, nthreads=0):
 def dct1_lines(n, per, gstride, lstride, es, data, l0, l1, nthreads=0):
     _check(_load().p3o_dct1_lines(n, per, gstride, lstride, es, _ptr(data), l0, l1,
                                   nthreads or nthreads_default()), "dct1_lines")
+
+
+# --- sampled outputs of the definition on full-size grids ---
+
+_TYPES = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.complex64): 2,
+          np.dtype(np.complex128): 3}
+
+
+class PhaseSum:
+    """Accumulates g[k][x] = sum_{z,y} A[z][y][x] exp(sign 2 pi i (a_k y/ny + b_k z/nz))
+    over z-chunks of an [nz][ny][nx] array fed in order (so a full-size array
+    never has to be on the host at once)."""
+
+    def __init__(self, nx, ny, nz, a, b, sign, nthreads=0):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.a = np.ascontiguousarray(a, dtype=np.int64)
+        self.b = np.ascontiguousarray(b, dtype=np.int64)
+        self.sign = sign
+        self.g = np.zeros((len(self.a), nx), dtype=np.complex128)
+        self.nthreads = nthreads or nthreads_default()
+
+    def add(self, chunk, z0):
+        chunk = np.ascontiguousarray(chunk)
+        z1 = z0 + chunk.shape[0]
+        rc = _load().p3o_phase_sum_yz(self.nx, self.ny, self.nz, _ptr(chunk), _TYPES[chunk.dtype], z0, z1,
+                                      len(self.a), _ptr(self.a), _ptr(self.b), self.sign, _ptr(self.g),
+                                      self.nthreads)
+        _check(rc, "phase_sum_yz")
+
+
+def forward_lines(g, nx):
+    """Finish sampled forward lines: F[kx] = DFT_x(g)[kx], kx < H."""
+    return np.stack([fft1d(row, -1)[:half(nx)] for row in g])
+
+
+def backward_rows(g, nx):
+    """Finish sampled inverse rows: the weighted c2r of each accumulated line."""
+    H = half(nx)
+    G = np.ascontiguousarray(g[:, :H], dtype=np.complex128)
+    out = np.zeros((G.shape[0], nx))
+    x_c2r_rows(nx, G.reshape(-1), out.reshape(-1), 0, G.shape[0])
+    return out

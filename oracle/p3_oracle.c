@@ -407,6 +407,75 @@ int p3o_forward(long nx, long ny, long nz, int ty, int tz,
     return yz_pass(nx, ny, nz, 2, tz, -1, F, nthreads);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sampled outputs of the definition for full-size grids.                      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    long nx, ny, z0, z1;
+    const void* a;  /* chunk [z1-z0][ny][nx] of the given type */
+    int type;       /* 0 f32 real, 1 f64 real, 2 complex64, 3 complex128 */
+    const cplx* py; /* [ny] phases along y for one index pair */
+    const cplx* pz; /* [nz] phases along z (absolute z) */
+    cplx* g;        /* [nx] accumulator */
+} psum_ctx;
+
+static cplx load_at(const psum_ctx* c, size_t i)
+{
+    switch (c->type) {
+    case 0: return ((const float*)c->a)[i];
+    case 1: return ((const double*)c->a)[i];
+    case 2: { const float* p = (const float*)c->a + 2 * i; return p[0] + p[1] * I; }
+    default: return ((const cplx*)c->a)[i];
+    }
+}
+
+/* Each worker owns the x range [x0, x1) of the accumulator. */
+static void psum_lines(void* v, long x0, long x1)
+{
+    psum_ctx* c = (psum_ctx*)v;
+    for (long z = c->z0; z < c->z1; ++z)
+        for (long y = 0; y < c->ny; ++y) {
+            const size_t row = ((size_t)(z - c->z0) * (size_t)c->ny + (size_t)y) * (size_t)c->nx;
+            const cplx w = c->py[y] * c->pz[z];
+            for (long x = x0; x < x1; ++x) c->g[x] += w * load_at(c, row + (size_t)x);
+        }
+}
+
+/*
+ * Accumulate, for nk index pairs (a_k, b_k),
+ *   g[k][x] += sum_{z in [z0, z1)} sum_y A[z][y][x] exp(sign 2 pi i (a_k y/ny + b_k z/nz))
+ * over a z-chunk A (the rows [z0, z1) of an [nz][ny][nx] array).  With
+ * sign -1 and (a, b) = (ky, kz) this is the Y and Z part of the forward
+ * definition for one output line; with sign +1, a complex input and
+ * (a, b) = (y, z) it is the Y and Z part of the inverse for one real row.
+ */
+int p3o_phase_sum_yz(long nx, long ny, long nz, const void* chunk, int type, long z0, long z1,
+                     long nk, const long* a, const long* b, int sign, cplx* g, int nthreads)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || z0 < 0 || z1 < z0 || z1 > nz || nk < 1 || type < 0 || type > 3)
+        return -1;
+    cplx* ry = make_roots(ny, sign);
+    cplx* rz = make_roots(nz, sign);
+    cplx* py = (cplx*)malloc(sizeof(cplx) * (size_t)(nk * ny));
+    cplx* pz = (cplx*)malloc(sizeof(cplx) * (size_t)(nk * nz));
+    if (!ry || !rz || !py || !pz) { free(ry); free(rz); free(py); free(pz); return -2; }
+    for (long k = 0; k < nk; ++k) {
+        const long ak = ((a[k] % ny) + ny) % ny, bk = ((b[k] % nz) + nz) % nz;
+        for (long y = 0; y < ny; ++y) py[k * ny + y] = ry[(ak * y) % ny];
+        for (long z = 0; z < nz; ++z) pz[k * nz + z] = rz[(bk * z) % nz];
+    }
+    psum_ctx base = { nx, ny, z0, z1, chunk, type, NULL, NULL, NULL };
+    for (long k = 0; k < nk; ++k) {
+        psum_ctx c = base;
+        c.py = py + k * ny;
+        c.pz = pz + k * nz;
+        c.g = g + k * nx;
+        parallel_lines(psum_lines, &c, 0, nx, nthreads);
+    }
+    free(ry); free(rz); free(py); free(pz);
+    return 0;
+}
+
 /* Full inverse 3D transform: F [nz][ny][H] complex -> f [nz][ny][nx] real.
    F is not modified. */
 int p3o_backward(long nx, long ny, long nz, int ty, int tz,

@@ -99,8 +99,9 @@ def _rank_sum(cz: np.ndarray, cy: np.ndarray, cx: np.ndarray, device=None,
               dtype=np.float64):
     """Re sum_m cz[m, z] cy[m, y] cx[m, x] as a real [Nz][Ny][Nx] array.
 
-    Evaluated as a (Nz*Ny x M) by (M x Nx) product in FP64, either with numpy
-    on the host (device None) or with torch on a CUDA device, in z-chunks."""
+    Evaluated as a (Nz*Ny x M) by (M x Nx) product, either with numpy in FP64
+    on the host (device None) or with torch on a CUDA device in the output
+    precision, in z-chunks."""
     M, nz = cz.shape
     ny, nx = cy.shape[1], cx.shape[1]
     if device is None:
@@ -114,13 +115,15 @@ def _rank_sum(cz: np.ndarray, cy: np.ndarray, cx: np.ndarray, device=None,
         return out
     import torch
     tdt = {np.float32: torch.float32, np.float64: torch.float64}[np.dtype(dtype).type]
+    # evaluated in the output precision (full-precision FP32 products, no TF32)
+    torch.backends.cuda.matmul.allow_tf32 = False
     out = torch.empty((nz, ny, nx), dtype=tdt, device=device)
-    czr = torch.from_numpy(np.ascontiguousarray(cz.real)).to(device)
-    czi = torch.from_numpy(np.ascontiguousarray(cz.imag)).to(device)
-    cyr = torch.from_numpy(np.ascontiguousarray(cy.real)).to(device)
-    cyi = torch.from_numpy(np.ascontiguousarray(cy.imag)).to(device)
-    cxr = torch.from_numpy(np.ascontiguousarray(cx.real)).to(device)
-    cxi = torch.from_numpy(np.ascontiguousarray(cx.imag)).to(device)
+    czr = torch.from_numpy(np.ascontiguousarray(cz.real)).to(device=device, dtype=tdt)
+    czi = torch.from_numpy(np.ascontiguousarray(cz.imag)).to(device=device, dtype=tdt)
+    cyr = torch.from_numpy(np.ascontiguousarray(cy.real)).to(device=device, dtype=tdt)
+    cyi = torch.from_numpy(np.ascontiguousarray(cy.imag)).to(device=device, dtype=tdt)
+    cxr = torch.from_numpy(np.ascontiguousarray(cx.real)).to(device=device, dtype=tdt)
+    cxi = torch.from_numpy(np.ascontiguousarray(cx.imag)).to(device=device, dtype=tdt)
     zc = max(1, min(nz, (1 << 26) // max(1, ny * M)))
     for z0 in range(0, nz, zc):
         z1 = min(nz, z0 + zc)

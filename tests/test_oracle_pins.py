@@ -362,3 +362,26 @@ def test_planted_mistakes(tmp_path, name):
         if rel_l2(g, brute_backward_3d(G, nx)) > 1e-12:
             failures += 1
     assert failures > 0, "mutant %s passed every pin" % name
+
+
+def test_sampled_lines_match_brute_force():
+    """PhaseSum + forward_lines / backward_rows (used for full-size parity)
+    against the brute-force 3D sums, with chunked accumulation over z."""
+    nz, ny, nx = 7, 6, 10
+    f = rand_real((nz, ny, nx), 21)
+    ref = brute_forward_3d(f)
+    pairs = [(0, 0), (5, 6), (2, 3)]
+    ps = O.PhaseSum(nx, ny, nz, [p[0] for p in pairs], [p[1] for p in pairs], -1)
+    for z0 in range(0, nz, 3):
+        ps.add(f[z0:z0 + 3], z0)
+    lines = O.forward_lines(ps.g, nx)
+    for i, (ky, kz) in enumerate(pairs):
+        assert rel_l2(lines[i], ref[kz, ky, :]) < 1e-13
+    F = rand_cplx((nz, ny, nx // 2 + 1), 22)
+    refb = brute_backward_3d(F, nx)
+    pts = [(0, 0), (4, 6), (5, 1)]
+    ps = O.PhaseSum(nx // 2 + 1, ny, nz, [p[0] for p in pts], [p[1] for p in pts], +1)
+    ps.add(F, 0)
+    rows = O.backward_rows(ps.g, nx)
+    for i, (y, z) in enumerate(pts):
+        assert rel_l2(rows[i], refb[z, y, :]) < 1e-13
