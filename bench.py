@@ -169,9 +169,13 @@ def traffic_record(kernel_name):
             rec = json.load(f)
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1905_02803_gb300", "csrc", "p3_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("kernel_source_sha256_16") != h:
+    h = hashlib.sha256()
+    for rel in rec.get("kernel_sources", []):
+        try:
+            h.update(open(os.path.join(ROOT, rel), "rb").read())
+        except OSError:
+            return None
+    if not rec.get("kernel_sources") or rec.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
         return None
     ent = rec.get("stages", {}).get(kernel_name)
     return None if ent is None else float(ent)
