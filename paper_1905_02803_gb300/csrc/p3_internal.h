@@ -84,6 +84,8 @@ struct StageArgs {
     // i * B + l.
     long long gcount;
     int glen;
+    // > 0: persistent pipelined kernel, launched with at most this many CTAs
+    int persist;
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.

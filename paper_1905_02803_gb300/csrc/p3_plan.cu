@@ -554,10 +554,23 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         for (auto& s : P->st[d]) {
             const StageArgs& a = s.a;
             std::string rs;
-            const int np = a.blue ? a.mpass : a.npass;
-            for (int i = 0; i < np; ++i) {
-                rs += std::to_string(a.blue ? a.mrad[i] : a.rad[i]);
-                if (i + 1 < np) rs += "x";
+            if (a.kern != p3::KIND_GENERIC) {
+                // power-of-two kernels: radix E = nfft / tpl while it divides, then the rest
+                const int E = a.nfft / a.tpl;
+                int n = a.nfft;
+                while (n % E == 0 && n >= E) {
+                    rs += std::to_string(E) + "x";
+                    n /= E;
+                }
+                if (n > 1) rs += std::to_string(n) + "x";
+                rs.pop_back();
+                if (a.persist > 0) rs += " persistent_ctas=" + std::to_string(a.persist);
+            } else {
+                const int np = a.blue ? a.mpass : a.npass;
+                for (int i = 0; i < np; ++i) {
+                    rs += std::to_string(a.blue ? a.mrad[i] : a.rad[i]);
+                    if (i + 1 < np) rs += "x";
+                }
             }
             if (rs.empty()) rs = "-";
             snprintf(line, sizeof(line),

@@ -5,16 +5,26 @@
 
 namespace p3 {
 
-void* pow2_pick_f32(int kind, int N, bool inv, bool dct);
-void* pow2_pick_f64(int kind, int N, bool inv, bool dct);
-void pow2_shape_f32(int kind, int N, int* B, int* tpl, size_t* smem);
-void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem);
+void* pow2_pick_f32(int kind, int N, bool inv, bool dct, bool pl);
+void* pow2_pick_f64(int kind, int N, bool inv, bool dct, bool pl);
+void pow2_shape_f32(int kind, int N, int* B, int* tpl, size_t* smem, int* pl);
+void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem, int* pl);
 
 namespace {
 bool is_pow2_in_range(int n) { return n >= 64 && n <= 4096 && (n & (n - 1)) == 0; }
 }  // namespace
 
+static bool configure(StageArgs& a, size_t csize);
+
 bool pow2_configure(StageArgs& a, size_t csize)
+{
+    StageArgs b = a;  // a keeps its generic configuration unless this succeeds
+    if (!configure(b, csize)) return false;
+    a = b;
+    return true;
+}
+
+static bool configure(StageArgs& a, size_t csize)
 {
     if (a.blue) return false;
     const int N = a.nfft;
@@ -34,16 +44,32 @@ bool pow2_configure(StageArgs& a, size_t csize)
     } else {
         return false;
     }
-    int B = 1, tpl = 1;
+    int B = 1, tpl = 1, pl = 0;
     size_t smem = 0;
-    if (f32) pow2_shape_f32(kind, N, &B, &tpl, &smem);
-    else pow2_shape_f64(kind, N, &B, &tpl, &smem);
+    if (f32) pow2_shape_f32(kind, N, &B, &tpl, &smem, &pl);
+    else pow2_shape_f64(kind, N, &B, &tpl, &smem, &pl);
     a.B = B;
     a.LDB = B;
     a.tpl = tpl;
     a.threads = B * tpl;
     a.smem = smem;
     a.kern = kind;
+    a.persist = 0;
+    if (pl) {
+        // persistent grid: resident CTAs per SM times the SM count
+        void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, a.op == OP_DCT1, true)
+                       : pow2_pick_f64(kind, N, a.sign > 0, a.op == OP_DCT1, true);
+        int dev = 0, sms = 0, per = 0;
+        if (fn && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, a.threads, a.smem) == cudaSuccess && per > 0) {
+            a.persist = sms * per;
+        } else {
+            cudaGetLastError();
+            return false;
+        }
+    }
     return true;
 }
 
@@ -53,23 +79,25 @@ cudaError_t pow2_prepare()
         for (int kind = KIND_COL_DD; kind <= KIND_ROW_C2R; ++kind)
             for (int N = 64; N <= 4096; N *= 2)
                 for (int inv = 0; inv < 2; ++inv)
-                    for (int dct = 0; dct < 2; ++dct) {
-                        void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, dct) : pow2_pick_f64(kind, N, inv, dct);
-                        if (!fn) continue;
-                        cudaError_t e =
-                            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-                        if (e != cudaSuccess) return e;
-                    }
+                    for (int dct = 0; dct < 2; ++dct)
+                        for (int pl = 0; pl < 2; ++pl) {
+                            void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, dct, pl) : pow2_pick_f64(kind, N, inv, dct, pl);
+                            if (!fn) continue;
+                            cudaError_t e =
+                                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                            if (e != cudaSuccess) return e;
+                        }
     return cudaSuccess;
 }
 
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
 {
-    const bool inv = a.sign > 0, dct = a.op == OP_DCT1;
-    void* fn = f32 ? pow2_pick_f32(a.kern, a.nfft, inv, dct) : pow2_pick_f64(a.kern, a.nfft, inv, dct);
+    const bool inv = a.sign > 0, dct = a.op == OP_DCT1, pl = a.persist > 0;
+    void* fn = f32 ? pow2_pick_f32(a.kern, a.nfft, inv, dct, pl) : pow2_pick_f64(a.kern, a.nfft, inv, dct, pl);
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;
-    const long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;
+    long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;
+    if (pl && grid > a.persist) grid = a.persist;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<StageArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(a.threads), args, a.smem, st);
