@@ -551,6 +551,10 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     // ---- description ----------------------------------------------------------
     char line[512];
     for (int d = 0; d < 2; ++d) {
+        std::string groups;  // one timing group per stage launch, in order
+        for (auto& s : P->st[d]) groups += (groups.empty() ? "" : ",") + std::string(s.name);
+        snprintf(line, sizeof(line), "%s groups=%s\n", d == 0 ? "fwd" : "bwd", groups.c_str());
+        P->desc += line;
         for (auto& s : P->st[d]) {
             const StageArgs& a = s.a;
             std::string rs;

@@ -91,9 +91,12 @@ template <class T> struct CxT;
 template <> struct CxT<float> { typedef float2 t; };
 template <> struct CxT<double> { typedef double2 t; };
 
+#ifndef P3_E32_MINB
+#define P3_E32_MINB 2
+#endif
 template <int NT, int CSIZE, int E> struct MinBlocks {
     static constexpr int value =
-        CSIZE == 8 ? (E == 32 ? (NT >= 512 ? 1 : 2) : (NT >= 512 ? 2 : 3)) : (NT >= 512 ? 1 : 2);
+        CSIZE == 8 ? (E == 32 ? (NT >= 512 ? 1 : P3_E32_MINB) : (NT >= 512 ? 2 : 3)) : (NT >= 512 ? 1 : 2);
 };
 
 __device__ __forceinline__ long long lbase(const LineMap& m, long long L)
