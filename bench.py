@@ -213,6 +213,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--report", action="store_true",
+                    help="measure every benchmark configuration (one JSON line each) instead of the 1024^3 line")
     ap.add_argument("--grid", default="1024",
                     help="grid edge N, or NX,NY,NZ (1024 is the benchmark workload; others are for profiling)")
     args = ap.parse_args()
@@ -225,6 +227,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.report:
+        run_report(args)
         return
 
     import numpy as np
@@ -380,6 +385,157 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+
+# ---------------------------------------------------------------------------
+# --report: every benchmark configuration, one JSON line each (not the
+# driver's single-line contract; used to fill profiles/configs_report.md)
+# ---------------------------------------------------------------------------
+REPORT_CONFIGS = [
+    # name, (nx, ny, nz), precision, ttypes, layout, input
+    ("32cube_f64", (32, 32, 32), "f64", ("fft", "fft", "fft"), "zyx", "config1"),
+    ("512cube_f32", (512, 512, 512), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
+    ("512cube_f64", (512, 512, 512), "f64", ("fft", "fft", "fft"), "zyx", "turbulence"),
+    ("1024cube_f32", (1024, 1024, 1024), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
+    ("2048cube_f32", (2048, 2048, 2048), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
+    ("channel_480x360x257_f64", (480, 360, 257), "f64", ("fft", "fft", "cheb"), "zyx", "channel"),
+]
+
+
+def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_1905_02803_gb300 import inputs
+    from paper_1905_02803_gb300 import p3dfft as P
+
+    nx, ny, nz = dims
+    plan = P.Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout)
+    npdt = np.float32 if prec == "f32" else np.float64
+    if kind == "config1":
+        x = torch.from_numpy(inputs.config1_field(nx, 0)[0]).to("cuda", plan.real_dtype)
+    elif kind == "channel":
+        x = inputs.channel_field(nx, ny, nz, seed=0, dtype=npdt, device=plan.device)
+    else:
+        x = inputs.turbulence_field((nz, ny, nx), seed=0, dtype=npdt, device=plan.device)
+    X = plan.empty_complex()
+    y = plan.empty_real()
+    ws = plan.workspace()
+    for _ in range(warmup):
+        plan.forward(x, X, ws)
+        plan.backward(X, y, ws)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        plan.forward(x, X, ws)
+        plan.backward(X, y, ws)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    e = 4 if prec == "f32" else 8
+    pair_bytes = sum(stage_model_bytes(nx, ny, nz, e))
+    peak, _ = peaks()
+    roof_ms = pair_bytes / (peak * 1e9) * 1e3
+    N = nx * ny * nz
+    gflops = 2 * 5 * N * math.log2(N) / (ms * 1e-3) / 1e9
+    tt = tuple({"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY}[t] for t in ttypes)
+    # parity: full oracle where it fits, else sampled lines (as the full-size tests)
+    t_or = None
+    if N <= 64 * 1024 * 1024:
+        xin = x.double().cpu().numpy()
+        tc = time.perf_counter()
+        ref = O.forward(xin, tt)
+        O.backward(ref, nx, tt)
+        t_or = (time.perf_counter() - tc) * 1e3
+        ref = O.to_zyx(ref) if layout == "zyx" else ref
+        got = X.cpu().numpy().astype(np.complex128)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        err_kind = "full rel-L2 vs oracle"
+    else:
+        pairs = [(0, 0), (1, 0), (3, 7), (ny // 2, nz - 1)]
+        ps = O.PhaseSum(nx, ny, nz, [p[0] for p in pairs], [p[1] for p in pairs], -1)
+        e_host = 0.0
+        for z0 in range(0, nz, 32):
+            blk = x[z0:z0 + 32].cpu().numpy()
+            e_host += float(np.sum(blk.astype(np.float64) ** 2))
+            ps.add(blk, z0)
+        ref = O.forward_lines(ps.g, nx)
+        e_line = N * e_host / (2.0 * ny * nz)
+        num = den = 0.0
+        for i, (ky, kz) in enumerate(pairs):
+            got = (X[:, ky, kz] if layout == "zyx" else X[kz, ky, :]).cpu().numpy().astype(np.complex128)
+            num += float(np.sum(np.abs(got - ref[i]) ** 2))
+            den += max(e_line, float(np.sum(np.abs(ref[i]) ** 2)))
+        err = math.sqrt(num / den)
+        err_kind = "sampled-line rel-L2 vs oracle (4 lines)"
+    num = den = 0.0
+    for z0 in range(0, nz, 64):  # chunked FP64 reductions (2048^3 arrays are 34 GB)
+        xd = x[z0:z0 + 64].double()
+        num += (torch.linalg.vector_norm(y[z0:z0 + 64].double() / plan.scale - xd) ** 2).item()
+        den += (torch.linalg.vector_norm(xd) ** 2).item()
+    rt = math.sqrt(num / den)
+    return {"config": name, "grid": list(dims), "precision": prec, "ttypes": list(ttypes), "layout": layout,
+            "ms": round(ms, 4), "gflops": round(gflops, 1), "stage_model_bytes": pair_bytes,
+            "hbm_roofline_ms": round(roof_ms, 4), "hbm_roofline_frac": round(roof_ms / ms, 4),
+            "rel_l2": err, "rel_l2_kind": err_kind, "round_trip_rel_l2": rt,
+            "oracle_ms_full": None if t_or is None else round(t_or, 1)}
+
+
+def _report_batch(steps, warmup):
+    """64 independent FP32 transforms of 7-smooth sizes, 64 plain plan launches."""
+    import numpy as np
+    import torch
+
+    from paper_1905_02803_gb300 import inputs
+    from paper_1905_02803_gb300 import p3dfft as P
+
+    dims = inputs.batch_dims(0)
+    plans, xs, Xs, ys = [], [], [], []
+    for k, (nx, ny, nz) in enumerate(dims):
+        p = P.Plan(nx, ny, nz, precision="f32", layout="zyx")
+        plans.append(p)
+        xs.append(torch.from_numpy(inputs.gaussian_field((nz, ny, nx), seed=k).astype(np.float32)).cuda())
+        Xs.append(p.empty_complex())
+        ys.append(p.empty_real())
+    def step():
+        for p, x, X, y in zip(plans, xs, Xs, ys):
+            p.forward(x, X)
+            p.backward(X, y)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    pair_bytes = sum(sum(stage_model_bytes(nx, ny, nz, 4)) for nx, ny, nz in dims)
+    peak, _ = peaks()
+    roof_ms = pair_bytes / (peak * 1e9) * 1e3
+    launches = sum(p.launches(0) + p.launches(1) for p in plans)
+    kinds = sorted({l.split()[2] for p in plans for l in p.describe().splitlines() if "kernel=" in l})
+    return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(ms, 4),
+            "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
+            "hbm_roofline_frac": round(roof_ms / ms, 4), "launches_per_step": launches, "kernels": kinds,
+            "mode": "64 separate plans, plain launches on one stream"}
+
+
+def run_report(args):
+    import torch
+    torch.cuda.set_device(0)
+    for c in REPORT_CONFIGS:
+        steps = 3 if c[1][0] >= 2048 else 20
+        r = _report_one(*c, steps=steps, warmup=3)
+        print(json.dumps(r), flush=True)
+        torch.cuda.empty_cache()
+    print(json.dumps(_report_batch(10, 2)), flush=True)
 
 
 if __name__ == "__main__":
