@@ -22,65 +22,72 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // One Stockham (autosort, decimation in time) pass of radix R over n points
-// of every tile line.  Butterfly j reads elements j + r n/R, multiplies by
+// of every tile line, from buffer src to buffer dst (ping-pong, so each
+// butterfly is read, transformed and written at once and only R values are
+// live).  Butterfly j reads elements j + r n/R, multiplies by
 // exp(-2 pi i (j mod Ns) r / (Ns R)), does a size-R DFT and writes
 // (j / Ns) Ns R + (j mod Ns) + r Ns.  Thread t of a line takes butterflies
-// t, t + tpl, ...; all reads finish (barrier) before any write.
+// t, t + tpl, ...; j / Ns and j mod Ns are updated incrementally.
 // ---------------------------------------------------------------------------
 template <class C, class T, int R>
-__device__ __noinline__ void pass_r(C* s, int LDB, int l, int t, int tpl, bool act, int n, int Ns,
-                                       const C* tw, int ts)
+__device__ __forceinline__ void pass_pp(const C* src, C* dst, int LDB, int l, int t, int tpl, int n, int Ns,
+                                        const C* tw, int ts)
 {
-    constexpr int BM = kVmax / R;
     const int nb = n / R;
     const int span = n / (Ns * R);
-    C v[BM][R];
+    int q = t / Ns, rr = t - q * Ns;
+    const int dq = tpl / Ns, dr = tpl - dq * Ns;
+    for (int j = t; j < nb; j += tpl) {
+        C v[R];
 #pragma unroll
-    for (int b = 0; b < BM; ++b) {
-        const int j = t + b * tpl;
-        if (act && j < nb) {
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * LDB + l];
+        const int k = rr * span;
+        if (k) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = s[(j + r * nb) * LDB + l];
-            const int k = (j % Ns) * span;
-            if (k) {
+            for (int r = 1; r < R; ++r) v[r] = mul(v[r], ldg(tw + (size_t)(k * r) * ts));
+        }
+        Dft<C, T, R>::run(v);
+        const int base = q * Ns * R + rr;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = mul(v[b][r], ldg(tw + (size_t)(k * r) * ts));
-            }
-            Dft<C, T, R>::run(v[b]);
+        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * LDB + l] = v[r];
+        rr += dr;
+        q += dq;
+        if (rr >= Ns) {
+            rr -= Ns;
+            ++q;
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < BM; ++b) {
-        const int j = t + b * tpl;
-        if (act && j < nb) {
-            const int base = (j / Ns) * Ns * R + (j % Ns);
-#pragma unroll
-            for (int r = 0; r < R; ++r) s[(base + r * Ns) * LDB + l] = v[b][r];
-        }
-    }
-    __syncthreads();
 }
 
+// All passes; the data starts in buf0 and the returned buffer holds the result.
 template <class C, class T>
-__device__ __forceinline__ void run_passes(C* s, int LDB, int l, int t, int tpl, bool act, int n, int npass,
-                                           const int* rad, const C* tw, int ts)
+__device__ __forceinline__ C* run_passes(C* buf0, C* buf1, int LDB, int l, int t, int tpl, bool act, int n,
+                                         int npass, const int* rad, const C* tw, int ts)
 {
     int Ns = 1;
+    C* src = buf0;
+    C* dst = buf1;
     for (int p = 0; p < npass; ++p) {
         const int R = rad[p];
-        switch (R) {
-        case 16: pass_r<C, T, 16>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 8: pass_r<C, T, 8>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 4: pass_r<C, T, 4>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 2: pass_r<C, T, 2>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 3: pass_r<C, T, 3>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 5: pass_r<C, T, 5>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        case 7: pass_r<C, T, 7>(s, LDB, l, t, tpl, act, n, Ns, tw, ts); break;
-        default: break;
+        if (act) {
+            switch (R) {
+            case 16: pass_pp<C, T, 16>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 8: pass_pp<C, T, 8>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 4: pass_pp<C, T, 4>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 2: pass_pp<C, T, 2>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 3: pass_pp<C, T, 3>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 5: pass_pp<C, T, 5>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            case 7: pass_pp<C, T, 7>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
+            default: break;
+            }
         }
+        __syncthreads();
         Ns *= R;
+        C* tmp = src;
+        src = dst;
+        dst = tmp;
     }
+    return src;
 }
 
 __device__ __forceinline__ long long line_base(const LineMap& m, long long L)
@@ -200,18 +207,18 @@ __device__ __forceinline__ void store_value(const StageArgs& a, const C* sl, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) stage_kernel(const __grid_constant__ StageArgs a)
+__global__ void __launch_bounds__(kMaxThreads, 2) stage_kernel(const __grid_constant__ StageArgs a)
 {
     typedef typename Cx<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
-
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int B = a.B, LDB = a.LDB;
     const long long L0 = (long long)blockIdx.x * B;
     const int nload = a.blue ? a.m : a.nfft;  // slots filled per line
     const int nfill = a.blue ? a.nfft : nload;  // slots taken from the input
+    C* s0 = reinterpret_cast<C*>(smem_raw);
+    C* s1 = s0 + (size_t)nload * LDB;  // second buffer of the ping-pong passes
 
     // ---- load: HBM -> shared memory ------------------------------------
     if (a.in_elem_fast) {
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(kMaxThreads) stage_kernel(const __grid_constan
             if (L >= a.nlines) break;
             const long long base = line_base(a.in, L);
             for (int e = lane; e < nload; e += 32)
-                s[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
+                s0[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
         }
     } else {
         const int l = tid & (B - 1);
@@ -229,31 +236,32 @@ __global__ void __launch_bounds__(kMaxThreads) stage_kernel(const __grid_constan
         if (L < a.nlines) {
             const long long base = line_base(a.in, L);
             for (int e = tid / B; e < nload; e += NT / B)
-                s[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
+                s0[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
         }
     }
     __syncthreads();
 
     // ---- FFT of every tile line in shared memory -----------------------
+    C* s = s0;
     {
         const int l = tid & (B - 1);
         const int t = tid / B;
         const bool act = tid < B * a.tpl;
         if (!a.blue) {
-            run_passes<C, T>(s, LDB, l, t, a.tpl, act, a.nfft, a.npass, a.rad, static_cast<const C*>(a.tw),
-                             a.twn / (a.nfft > 0 ? a.nfft : 1));
+            s = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.nfft, a.npass, a.rad,
+                                 static_cast<const C*>(a.tw), a.twn / (a.nfft > 0 ? a.nfft : 1));
         } else {
             // Bluestein: DFT_m, pointwise product with the filter spectrum,
             // inverse DFT_m as swp(DFT_m(swp(.))); the 1/m is folded into bhat.
             const C* twm = static_cast<const C*>(a.twm);
-            run_passes<C, T>(s, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
+            C* x = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
             const C* bh = static_cast<const C*>(a.bhat);
             for (int i = tid; i < a.m * B; i += NT) {
                 const int k = i / B, ll = i - k * B;
-                s[k * LDB + ll] = swp(mul(s[k * LDB + ll], ldg(bh + k)));
+                x[k * LDB + ll] = swp(mul(x[k * LDB + ll], ldg(bh + k)));
             }
             __syncthreads();
-            run_passes<C, T>(s, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
+            s = run_passes<C, T>(x, x == s0 ? s1 : s0, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
         }
     }
 

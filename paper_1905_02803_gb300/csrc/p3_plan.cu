@@ -148,15 +148,14 @@ bool factor(int n, std::vector<int>& rad)
     return m == 1 && (int)rad.size() <= p3::kMaxPasses;
 }
 
-// Threads per line so that no thread holds more than kVmax values in a pass.
+// Threads per line of the generic kernel: each thread takes about kVmax
+// values per pass (the passes loop over butterflies, so any count works).
 int threads_per_line(int n, const std::vector<int>& rad)
 {
-    int tpl = 1;
-    for (int R : rad) {
-        const int nb = n / R, bm = p3::kVmax / R;
-        const int need = (nb + bm - 1) / bm;
-        if (need > tpl) tpl = need;
-    }
+    (void)rad;
+    int tpl = (n + p3::kVmax - 1) / p3::kVmax;
+    if (tpl < 1) tpl = 1;
+    if (tpl > p3::kMaxThreads) tpl = p3::kMaxThreads;
     return tpl;
 }
 
@@ -267,10 +266,10 @@ void tile_setup(StageArgs& a, size_t csize)
 {
     const int len = a.blue ? a.m : (a.nfft > 0 ? a.nfft : 1);
     const bool elem = a.in_elem_fast || a.out_elem_fast;
-    const size_t cap = 96 * 1024;
+    const size_t cap = 100 * 1024;
     int B = pow2_floor(p3::kMaxThreads / a.tpl);
     if (B < 1) B = 1;
-    while (B > 1 && (size_t)len * (size_t)(B + 1) * csize > cap) B /= 2;
+    while (B > 1 && 2 * (size_t)len * (size_t)(B + 1) * csize > cap) B /= 2;
     const long long lim = pow2_ceil(a.nlines > 0 ? a.nlines : 1);
     if (B > lim) B = (int)lim;
     a.B = B;
@@ -278,7 +277,7 @@ void tile_setup(StageArgs& a, size_t csize)
     int th = B * a.tpl;
     th = (th + 31) / 32 * 32;
     a.threads = th;
-    a.smem = (size_t)len * (size_t)a.LDB * csize;
+    a.smem = 2 * (size_t)len * (size_t)a.LDB * csize;  // ping-pong buffers
     a.kern = p3::KIND_GENERIC;
     p3::pow2_configure(a, csize);
 }
