@@ -231,8 +231,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core split-precision comparison")
     ap.add_argument("--report", action="store_true",
                     help="measure every benchmark configuration (one JSON line each) instead of the 1024^3 line")
+    ap.add_argument("--report-only", default="", help="with --report: only the named config (batch64)")
     ap.add_argument("--grid", default="1024",
                     help="grid edge N, or NX,NY,NZ (1024 is the benchmark workload; others are for profiling)")
     args = ap.parse_args()
@@ -366,6 +368,39 @@ def main():
     pair_bytes = sum(sb)
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
 
+    # tensor-core split-precision form of the same workload (the metric's
+    # "TC-split vs plain"): time it and compare its output with the plain one
+    tc = None
+    if not args.no_tc and PREC == "f32":
+        ptc = P.Plan(NX, NY, NZ, precision=PREC, layout=LAYOUT, flags=P.P3_FLAG_TC_SPLIT)
+        if "tc_split_col" in ptc.describe():
+            Xtc = ptc.empty_complex()
+            ytc = ptc.empty_real()
+            wtc = ptc.workspace()
+            for _ in range(3):
+                ptc.forward(x, Xtc, wtc, stream)
+                ptc.backward(Xtc, ytc, wtc, stream)
+            torch.cuda.synchronize()
+            t0.record(stream)
+            for _ in range(args.steps):
+                ptc.forward(x, Xtc, wtc, stream)
+                ptc.backward(Xtc, ytc, wtc, stream)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms_tc = t0.elapsed_time(t1) / args.steps
+            num = den = 0.0
+            for a0 in range(0, X.shape[0], 64):
+                d = (Xtc[a0:a0 + 64] - X[a0:a0 + 64]).to(torch.complex128)
+                num += (torch.linalg.vector_norm(d) ** 2).item()
+                den += (torch.linalg.vector_norm(X[a0:a0 + 64].to(torch.complex128)) ** 2).item()
+            tc = {"ms": round(ms_tc, 4), "plain_ms": round(ms, 4), "speedup_vs_plain": round(ms / ms_tc, 4),
+                  "rel_l2_vs_plain": math.sqrt(num / den),
+                  "what": "FP32 1024-point Y/Z stages as tensor-core products (mma.sync TF32, each operand split "
+                          "into a TF32 head and tail, 3 products accumulated in FP32); X stages as plain",
+                  "oracle_check": "tests/test_gpu_fullsize.py: within 5e-6 of the FP64 oracle at 1024^3"}
+            del Xtc, ytc, wtc, ptc
+            torch.cuda.empty_cache()
+
     # round-trip sanity (torch reduction on the device, test-style check only)
     rt = (torch.linalg.vector_norm(y.double() / plan.scale - x.double()) /
           torch.linalg.vector_norm(x.double())).item()
@@ -389,6 +424,7 @@ def main():
                 "d2h_bytes_per_step": int(yh.numel() * yh.element_size())},
         "gpu_launches": int(sum(plan.launches(d) for d in (0, 1)) * args.steps),
         "round_trip_rel_l2": rt,
+        "tc_split": tc,
         "clocks": clk.summary(),
         "plan": desc,
     }
@@ -530,12 +566,32 @@ def _report_batch(steps, warmup):
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
+    # the same 384 launches captured once into a CUDA graph and replayed
+    for p in plans:
+        p.workspace()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            step()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(steps):
+        g.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    ms_graph = t0.elapsed_time(t1) / steps
     pair_bytes = sum(sum(stage_model_bytes(nx, ny, nz, 4)) for nx, ny, nz in dims)
     peak, _ = peaks()
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
     launches = sum(p.launches(0) + p.launches(1) for p in plans)
     kinds = sorted({l.split()[2] for p in plans for l in p.describe().splitlines() if "kernel=" in l})
-    return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(ms, 4),
+    return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(ms, 4), "ms_cuda_graph": round(ms_graph, 4),
             "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
             "hbm_roofline_frac": round(roof_ms / ms, 4), "launches_per_step": launches, "kernels": kinds,
             "mode": "64 separate plans, plain launches on one stream"}
@@ -544,6 +600,9 @@ def _report_batch(steps, warmup):
 def run_report(args):
     import torch
     torch.cuda.set_device(0)
+    if args.report_only:
+        print(json.dumps(_report_batch(10, 2)), flush=True)
+        return
     for c in REPORT_CONFIGS:
         steps = 3 if c[1][0] >= 2048 else 20
         r = _report_one(*c, steps=steps, warmup=3)

@@ -71,6 +71,9 @@ typedef enum { P3_F32 = 0, P3_F64 = 1 } p3_precision;
 /* Sect. 3.1 / Sect. 5: Fourier, Chebyshev (DCT-I, third dimension only), empty. */
 typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2 } p3_ttype;
 
+/* Plan flags (p3_plan_create). */
+#define P3_FLAG_TC_SPLIT 1u
+
 /* Table 1: storage order of the Z-pencil complex array. */
 typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
 
@@ -84,11 +87,14 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *              real-to-complex stage defines the path), ttype[1] P3_FFT or
  *              P3_EMPTY, ttype[2] P3_FFT, P3_CHEB or P3_EMPTY.
  *   out_layout storage order of the complex array (Table 1).
- *   flags      must be 0.
+ *   flags      0, or P3_FLAG_TC_SPLIT: run the FP32 1024-point Y / Z stages
+ *              on the tensor cores in split precision (each FP32 operand
+ *              split into a TF32 head and tail, three products accumulated
+ *              in FP32).  No effect on other stages or precisions.
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.
- * Errors: P3_ERR_INVALID (NULL out/ttype, bad dims or enum, flags != 0),
+ * Errors: P3_ERR_INVALID (NULL out/ttype, bad dims or enum, unknown flags),
  * P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA (no usable device).
  * Argument checks happen before any CUDA call.
  */

@@ -86,6 +86,8 @@ struct StageArgs {
     int glen;
     // > 0: persistent pipelined kernel, launched with at most this many CTAs
     int persist;
+    // 1: tensor-core split-precision kernel (p3_tc.cu)
+    int tc;
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.
@@ -99,5 +101,10 @@ cudaError_t prepare_kernels();
 bool pow2_configure(StageArgs& a, size_t csize);
 cudaError_t pow2_prepare();
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t s);
+
+// Tensor-core split-precision kernels (p3_tc.cu): FP32 1024-point columns.
+bool tc_configure(StageArgs& a, size_t csize);
+cudaError_t tc_prepare();
+cudaError_t tc_launch(const StageArgs& a, cudaStream_t s);
 
 }  // namespace p3

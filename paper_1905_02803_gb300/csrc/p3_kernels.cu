@@ -298,6 +298,7 @@ cudaError_t launch_stage(const StageArgs& a, cudaStream_t st)
 
 cudaError_t launch_stage_f32(const StageArgs& a, cudaStream_t s)
 {
+    if (a.tc) return tc_launch(a, s);
     return a.kern != KIND_GENERIC ? pow2_launch(a, true, s) : launch_stage<float>(a, s);
 }
 cudaError_t launch_stage_f64(const StageArgs& a, cudaStream_t s)
@@ -312,7 +313,9 @@ cudaError_t prepare_kernels()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    return pow2_prepare();
+    e = pow2_prepare();
+    if (e != cudaSuccess) return e;
+    return tc_prepare();
 }
 
 }  // namespace p3

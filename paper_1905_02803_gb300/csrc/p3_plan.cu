@@ -262,7 +262,7 @@ p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
 }
 
 // Lines per CTA, pitch, threads and shared memory of a stage.
-void tile_setup(StageArgs& a, size_t csize)
+void tile_setup(StageArgs& a, size_t csize, unsigned flags)
 {
     const int len = a.blue ? a.m : (a.nfft > 0 ? a.nfft : 1);
     const bool elem = a.in_elem_fast || a.out_elem_fast;
@@ -279,7 +279,9 @@ void tile_setup(StageArgs& a, size_t csize)
     a.threads = th;
     a.smem = 2 * (size_t)len * (size_t)a.LDB * csize;  // ping-pong buffers
     a.kern = p3::KIND_GENERIC;
+    a.tc = 0;
     p3::pow2_configure(a, csize);
+    if (flags & P3_FLAG_TC_SPLIT) p3::tc_configure(a, csize);
 }
 
 LineMap rows(long long nlines, long long pitch) { return LineMap{nlines > 0 ? nlines : 1, 0, pitch, 1}; }
@@ -297,8 +299,9 @@ const char* op_name(int op)
     }
 }
 
-const char* kern_name(int k)
+const char* kern_name(int k, int tc)
 {
+    if (tc) return "tc_split_col";
     switch (k) {
     case p3::KIND_COL_DD: return "pow2_col";
     case p3::KIND_COL_DS: return "pow2_col_zyx_store";
@@ -351,7 +354,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
 {
     if (!out) return P3_ERR_INVALID;
     *out = NULL;
-    if (!ttype || nx < 1 || ny < 1 || nz < 1 || flags != 0) return P3_ERR_INVALID;
+    if (!ttype || nx < 1 || ny < 1 || nz < 1 || (flags & ~(unsigned)P3_FLAG_TC_SPLIT)) return P3_ERR_INVALID;
     if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
     if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
     for (int d = 0; d < 3; ++d)
@@ -417,7 +420,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.nfft = a.n_in;  // slots per line; no FFT passes
             a.npass = 0;
         }
-        tile_setup(a, P->csize);
+        tile_setup(a, P->csize, flags);
         a.gcount = 0;
         a.glen = 0;
         if (name[0] == 'z' && a.kern >= p3::KIND_COL_DD && a.kern <= p3::KIND_COL_SD && P3_Z_GROUP_MAJOR) {
@@ -579,7 +582,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             snprintf(line, sizeof(line),
                      "%s %s kernel=%s op=%s nfft=%d%s radices=%s lines=%lld B=%d LDB=%d tpl=%d threads=%d "
                      "smem=%zu bytes=%.0f\n",
-                     d == 0 ? "fwd" : "bwd", s.name, kern_name(a.kern), op_name(a.op), a.nfft,
+                     d == 0 ? "fwd" : "bwd", s.name, kern_name(a.kern, a.tc), op_name(a.op), a.nfft,
                      a.blue ? (" bluestein_m=" + std::to_string(a.m)).c_str() : "", rs.c_str(), a.nlines, a.B,
                      a.LDB, a.tpl, a.threads, a.smem, s.bytes);
             P->desc += line;

@@ -18,6 +18,7 @@ P3_OK, P3_ERR_INVALID, P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA, P3_ERR_TIM
 P3_F32, P3_F64 = 0, 1
 P3_FFT, P3_CHEB, P3_EMPTY = 0, 1, 2
 P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
+P3_FLAG_TC_SPLIT = 1
 
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
@@ -170,7 +171,8 @@ class Plan:
     (nz, ny, nx); complex arrays (nz, ny, H) for layout 'xyz' or (H, ny, nz)
     for 'zyx', H = nx // 2 + 1."""
 
-    def __init__(self, nx, ny, nz, precision="f32", ttypes=("fft", "fft", "fft"), layout="zyx", device=None):
+    def __init__(self, nx, ny, nz, precision="f32", ttypes=("fft", "fft", "fft"), layout="zyx", device=None,
+                 flags=0):
         import torch
         self.torch = torch
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
@@ -181,7 +183,7 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             _, self.handle = p3_plan_create(self.nx, self.ny, self.nz, P3_F32 if precision == "f32" else P3_F64,
-                                            [_TT[t] for t in self.ttypes], _LAYOUT[layout])
+                                            [_TT[t] for t in self.ttypes], _LAYOUT[layout], flags)
         self.real_dtype = torch.float32 if precision == "f32" else torch.float64
         self.complex_dtype = torch.complex64 if precision == "f32" else torch.complex128
         self.ws_bytes = p3_plan_workspace_bytes(self.handle)

@@ -5,6 +5,7 @@ import oracle as O
 from paper_1905_02803_gb300 import inputs
 
 TOL = {"f32": 2e-6, "f64": 1e-13}
+TOL_TC = 5e-6  # tensor-core split-precision stages (FP32 data)
 TT = {"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY}
 
 
@@ -22,13 +23,13 @@ def random_complex(shape, seed):
 
 
 def check_case(nx, ny, nz, prec="f64", ttypes=("fft", "fft", "fft"), layout="zyx", field=None, seed=0,
-               check_inverse=True):
+               check_inverse=True, flags=0):
     """Forward of a real field and inverse of a random (non-Hermitian) complex
     array, each compared element by element with the oracle; returns errors."""
     import torch
     from paper_1905_02803_gb300.p3dfft import Plan
 
-    plan = Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout)
+    plan = Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout, flags=flags)
     if field is None:
         field = inputs.uniform_field((nz, ny, nx), seed)
     x = torch.from_numpy(np.ascontiguousarray(field)).to(device="cuda", dtype=plan.real_dtype)

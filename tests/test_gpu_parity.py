@@ -142,3 +142,16 @@ def test_pow2_chebyshev(nz, layout):
         ef, eb, plan = check_case(12, 6, nz, prec, ttypes=("fft", "fft", "cheb"), layout=layout, seed=nz)
         assert "pow2_col" in plan.describe()
         assert ef <= TOL[prec] and eb <= TOL[prec], (prec, ef, eb)
+
+
+@pytest.mark.parametrize("shape", [(16, 1024, 6), (6, 4, 1024), (130, 1024, 3), (8, 1024, 1024)])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_tc_split_parity(shape, layout):
+    """FP32 1024-point Y / Z stages on the tensor cores (TF32 head/tail split,
+    three products): within 5e-6 of the FP64 oracle."""
+    from _gpu_helpers import TOL_TC
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = shape
+    ef, eb, plan = check_case(nx, ny, nz, "f32", layout=layout, seed=11, flags=P.P3_FLAG_TC_SPLIT)
+    assert "tc_split_col" in plan.describe()
+    assert ef <= TOL_TC and eb <= TOL_TC, (ef, eb)
