@@ -4,7 +4,7 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  It shares no code with the CUDA library.
 """
 from .oracle import (  # noqa: F401
-    FFT, CHEB, EMPTY, forward, backward, fft1d, dct1, to_zyx, from_zyx,
-    x_r2c_rows, x_c2r_rows, c2c_lines, dct1_lines, scale, half, nthreads_default,
+    FFT, CHEB, EMPTY, SINE, forward, backward, fft1d, dct1, dst1, to_zyx, from_zyx,
+    x_r2c_rows, x_c2r_rows, c2c_lines, dct1_lines, dst1_lines, scale, half, nthreads_default,
     PhaseSum, forward_lines, backward_rows,
 )

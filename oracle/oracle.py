@@ -8,7 +8,8 @@ the whole grid):
   complex arrays  numpy complex128 [Nz][Ny][H], H = Nx//2 + 1  (XYZ storage)
   ZYX storage     [H][Ny][Nz] (the STRIDE1 Z-pencil of Table 1), produced here
                   only by the trivial permutation to_zyx().
-Transform types per dimension: FFT, CHEB (DCT-I, third dimension only), EMPTY.
+Transform types per dimension: FFT, CHEB (DCT-I, third dimension only), EMPTY,
+SINE (DST-I, third dimension only).
 """
 import ctypes
 import os
@@ -17,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-FFT, CHEB, EMPTY = 0, 1, 2
+FFT, CHEB, EMPTY, SINE = 0, 1, 2, 3
 
 _lib = None
 
@@ -42,11 +43,13 @@ def _load():
     lib.p3o_x_c2r_rows.argtypes = [L, P, P, L, L, I]
     lib.p3o_c2c_lines.argtypes = [L, L, L, L, L, P, L, L, I, I]
     lib.p3o_dct1_lines.argtypes = [L, L, L, L, L, P, L, L, I]
+    lib.p3o_dst1.argtypes = [L, P, P]
+    lib.p3o_dst1_lines.argtypes = [L, L, L, L, L, P, L, L, I]
     lib.p3o_forward.argtypes = [L, L, L, I, I, P, P, I]
     lib.p3o_phase_sum_yz.argtypes = [L, L, L, P, I, L, L, L, P, P, I, P, I]
     lib.p3o_backward.argtypes = [L, L, L, I, I, P, P, I]
     for name in ("p3o_fft1d", "p3o_dct1", "p3o_x_r2c_rows", "p3o_x_c2r_rows",
-                 "p3o_c2c_lines", "p3o_dct1_lines", "p3o_forward", "p3o_backward", "p3o_phase_sum_yz"):
+                 "p3o_c2c_lines", "p3o_dct1_lines", "p3o_forward", "p3o_backward", "p3o_phase_sum_yz", "p3o_dst1", "p3o_dst1_lines"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -69,10 +72,11 @@ def half(nx: int) -> int:
 def scale(nx: int, ny: int, nz: int, ttypes=(FFT, FFT, FFT)) -> float:
     """Round-trip factor of the unnormalised pair (Sect. 4.1 'apart from a
     scale factor'): the product over dimensions of n for FFT, 2(n-1) for
-    Chebyshev (DCT-I applied twice) and 1 for the empty transform."""
+    Chebyshev (DCT-I applied twice), 2(n+1) for the sine transform (DST-I
+    applied twice) and 1 for the empty transform."""
     s = float(nx)
     for n, t in ((ny, ttypes[1]), (nz, ttypes[2])):
-        s *= {FFT: float(n), CHEB: 2.0 * (n - 1), EMPTY: 1.0}[t]
+        s *= {FFT: float(n), CHEB: 2.0 * (n - 1), EMPTY: 1.0, SINE: 2.0 * (n + 1)}[t]
     return s
 
 
@@ -87,6 +91,13 @@ def dct1(x) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.complex128)
     out = np.empty_like(x)
     _check(_load().p3o_dct1(x.size, _ptr(x), _ptr(out)), "dct1")
+    return out
+
+
+def dst1(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.empty_like(x)
+    _check(_load().p3o_dst1(x.size, _ptr(x), _ptr(out)), "dst1")
     return out
 
 
@@ -139,6 +150,11 @@ def x_c2r_rows(nx, F_flat, f_flat, r0, r1, nthreads=0):
 def c2c_lines(n, per, gstride, lstride, es, data, l0, l1, sign, nthreads=0):
     _check(_load().p3o_c2c_lines(n, per, gstride, lstride, es, _ptr(data), l0, l1,
                                  sign, nthreads or nthreads_default()), "c2c_lines")
+
+
+def dst1_lines(n, per, gstride, lstride, es, data, l0, l1, nthreads=0):
+    _check(_load().p3o_dst1_lines(n, per, gstride, lstride, es, _ptr(data), l0, l1,
+                                  nthreads or nthreads_default()), "dst1_lines")
 
 
 def dct1_lines(n, per, gstride, lstride, es, data, l0, l1, nthreads=0):

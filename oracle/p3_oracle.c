@@ -19,6 +19,11 @@
  *             points:  Y_n = x_0 + (-1)^n x_M + 2 sum_{j=1}^{M-1} x_j cos(pi j n/M),
  *             M = Nz-1, applied to real and imaginary parts alike, evaluated
  *             as the direct O(M^2) sum.
+ *   Z may instead be the sine transform (the "sine" of Sect. 3.1's
+ *             sine/cosine transforms), taken as the unnormalised DST-I of the
+ *             Nz interior points of a Dirichlet grid:
+ *             Y_k = 2 sum_{j=0}^{Nz-1} x_j sin(pi (j+1)(k+1)/(Nz+1)),
+ *             again as the direct O(Nz^2) sum.
  *   Y or Z may be the "empty" (identity) transform (Sect. 3.1).
  *   backward: the reverse order (Z, Y inverse with the + sign, then X c2r),
  *             where the X c2r of a line is f[x] = Re sum_{k<H} w_k F[k]
@@ -47,7 +52,7 @@
 
 typedef double complex cplx;
 
-enum { P3O_FFT = 0, P3O_CHEB = 1, P3O_EMPTY = 2 };
+enum { P3O_FFT = 0, P3O_CHEB = 1, P3O_EMPTY = 2, P3O_SINE = 3 };
 
 /* ------------------------------------------------------------------------- */
 /* Roots of unity: roots[t] = exp(sign * 2 pi i t / n), t in [0, n).           */
@@ -289,6 +294,41 @@ static double* make_cheb_cos(long M)
     return c;
 }
 
+/* --- complex lines: in-place DST-I (direct sum) along one axis ---------- */
+typedef struct {
+    long n; /* points per line */
+    lines_t g;
+    cplx* data;
+    const double* sinv; /* sin(pi t / (n+1)), t in [0, 2(n+1)) */
+} dst_ctx;
+
+static void dst1_lines(void* c, long l0, long l1)
+{
+    dst_ctx* k = (dst_ctx*)c;
+    long n = k->n, P = 2 * (n + 1);
+    cplx* line = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    for (long L = l0; L < l1; ++L) {
+        cplx* p = k->data + line_base(&k->g, L);
+        for (long e = 0; e < n; ++e) line[e] = p[e * k->g.es];
+        for (long q = 0; q < n; ++q) {
+            cplx acc = 0;
+            for (long j = 0; j < n; ++j) acc += 2.0 * k->sinv[((j + 1) * (q + 1)) % P] * line[j];
+            p[q * k->g.es] = acc;
+        }
+    }
+    free(line);
+}
+
+static double* make_sine(long n)
+{
+    long P = 2 * (n + 1);
+    double* v = (double*)malloc(sizeof(double) * (size_t)P);
+    if (!v) return NULL;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (long t = 0; t < P; ++t) v[t] = (double)sinl(pi * (long double)t / (long double)(n + 1));
+    return v;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Public entry points (plain C ABI, called through ctypes by the tests).      */
 /* Return 0 on success, -1 on bad arguments, -2 on allocation failure.         */
@@ -320,6 +360,22 @@ int p3o_dct1(long n, const cplx* in, cplx* out)
     memcpy(out, buf, sizeof(cplx) * (size_t)n);
     free(buf);
     free(cosv);
+    return 0;
+}
+
+/* 1D unnormalised DST-I of n complex points (direct sum). */
+int p3o_dst1(long n, const cplx* in, cplx* out)
+{
+    if (n < 1) return -1;
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    double* sinv = make_sine(n);
+    if (!buf || !sinv) { free(buf); free(sinv); return -2; }
+    memcpy(buf, in, sizeof(cplx) * (size_t)n);
+    dst_ctx k = { n, { 1, 0, 0, 1 }, buf, sinv };
+    dst1_lines(&k, 0, 1);
+    memcpy(out, buf, sizeof(cplx) * (size_t)n);
+    free(buf);
+    free(sinv);
     return 0;
 }
 
@@ -374,6 +430,19 @@ int p3o_dct1_lines(long n, long per, long gstride, long lstride, long es,
     return 0;
 }
 
+/* In-place DST-I of lines [l0, l1) of n points; addressing as above. */
+int p3o_dst1_lines(long n, long per, long gstride, long lstride, long es,
+                   cplx* data, long l0, long l1, int nthreads)
+{
+    if (n < 1 || per < 1 || l0 < 0 || l1 < l0) return -1;
+    double* sinv = make_sine(n);
+    if (!sinv) return -2;
+    dst_ctx k = { n, { per, gstride, lstride, es }, data, sinv };
+    parallel_lines(dst1_lines, &k, l0, l1, nthreads);
+    free(sinv);
+    return 0;
+}
+
 /* Third-dimension / second-dimension pass over a whole XYZ complex array. */
 static int yz_pass(long nx, long ny, long nz, int axis, int ttype, int sign,
                    cplx* F, int nthreads)
@@ -389,6 +458,8 @@ static int yz_pass(long nx, long ny, long nz, int axis, int ttype, int sign,
         return p3o_c2c_lines(nz, H * ny, 0, 1, ny * H, F, 0, H * ny, sign, nthreads);
     if (ttype == P3O_CHEB)
         return p3o_dct1_lines(nz, H * ny, 0, 1, ny * H, F, 0, H * ny, nthreads);
+    if (ttype == P3O_SINE)
+        return p3o_dst1_lines(nz, H * ny, 0, 1, ny * H, F, 0, H * ny, nthreads);
     return -1;
 }
 
@@ -398,7 +469,7 @@ int p3o_forward(long nx, long ny, long nz, int ty, int tz,
 {
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     if (ty != P3O_FFT && ty != P3O_EMPTY) return -1;
-    if (tz != P3O_FFT && tz != P3O_CHEB && tz != P3O_EMPTY) return -1;
+    if (tz != P3O_FFT && tz != P3O_CHEB && tz != P3O_EMPTY && tz != P3O_SINE) return -1;
     if (tz == P3O_CHEB && nz < 2) return -1;
     int rc = p3o_x_r2c_rows(nx, f, F, 0, ny * nz, nthreads);
     if (rc) return rc;
@@ -483,7 +554,7 @@ int p3o_backward(long nx, long ny, long nz, int ty, int tz,
 {
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     if (ty != P3O_FFT && ty != P3O_EMPTY) return -1;
-    if (tz != P3O_FFT && tz != P3O_CHEB && tz != P3O_EMPTY) return -1;
+    if (tz != P3O_FFT && tz != P3O_CHEB && tz != P3O_EMPTY && tz != P3O_SINE) return -1;
     if (tz == P3O_CHEB && nz < 2) return -1;
     long H = nx / 2 + 1;
     size_t cnt = (size_t)H * (size_t)ny * (size_t)nz;

@@ -50,9 +50,13 @@ def brute_forward_3d(f, ttz="fft"):
         num = num + np.outer(kz.ravel(), z.ravel()) * (nx * ny)
         P = np.exp(-2j * math.pi * np.mod(num, den) / den)
         return (P @ f.ravel()).reshape(nz, ny, H)
+    P = np.exp(-2j * math.pi * np.mod(num, den) / den)
+    if ttz == "sine":
+        # DST-I in z: weight 2 sin(pi (z+1)(kz+1) / (nz+1))
+        S = 2 * np.sin(math.pi * np.mod(np.outer(kz.ravel() + 1, z.ravel() + 1), 2 * (nz + 1)) / (nz + 1))
+        return ((P * S) @ f.ravel()).reshape(nz, ny, H)
     # Chebyshev in z: weight c_j cos(pi j n / M) with c_0 = c_M = 1, else 2
     M = nz - 1
-    P = np.exp(-2j * math.pi * np.mod(num, den) / den)
     w = np.where((z.ravel() == 0) | (z.ravel() == M), 1.0, 2.0)
     C = w[None, :] * np.cos(math.pi * np.mod(np.outer(kz.ravel(), z.ravel()), 2 * M) / M)
     return ((P * C) @ f.ravel()).reshape(nz, ny, H)
@@ -132,6 +136,13 @@ def test_forward_chebyshev_matches_brute_force(shape):
     f = rand_real(shape, 3)
     got = O.forward(f, (O.FFT, O.FFT, O.CHEB))
     assert rel_l2(got, brute_forward_3d(f, "cheb")) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(9, 5, 6), (1, 4, 3), (2, 3, 4), (7, 2, 5)])
+def test_forward_sine_matches_brute_force(shape):
+    f = rand_real(shape, 3)
+    got = O.forward(f, (O.FFT, O.FFT, O.SINE))
+    assert rel_l2(got, brute_forward_3d(f, "sine")) < 1e-13
 
 
 def test_empty_transforms_are_identity_in_their_dimension():
@@ -219,6 +230,41 @@ def test_dct1_self_inverse():
         assert rel_l2(O.dct1(O.dct1(x)), 2 * (npts - 1) * x) < 1e-13
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 63, 100])
+def test_dst1_sine_mode_is_a_delta(n):
+    """sin(pi m (j+1)/(n+1)) is the m-th discrete sine mode: its DST-I is
+    (n+1) at k = m-1 and 0 elsewhere (orthogonality of the sine basis)."""
+    j = np.arange(n)
+    for m in sorted({1, (n + 1) // 2, n}):
+        x = np.sin(math.pi * m * (j + 1) / (n + 1)).astype(complex)
+        expect = np.zeros(n, complex)
+        expect[m - 1] = n + 1
+        assert np.abs(O.dst1(x) - expect).max() < 1e-12 * (n + 1)
+
+
+def test_dst1_self_inverse():
+    for npts in (1, 2, 5, 31, 255):
+        x = rand_cplx((npts,), npts + 3)
+        assert rel_l2(O.dst1(O.dst1(x)), 2 * (npts + 1) * x) < 1e-13
+
+
+def test_dst1_odd_extension_identity():
+    """The DST-I of x equals i times bins 1..n of the DFT of the odd
+    extension [0, x, 0, -reversed(x)] of length 2(n+1)."""
+    for n in (1, 6, 15, 40):
+        x = rand_cplx((n,), n + 40)
+        z = np.concatenate([[0], x, [0], -x[::-1]])
+        assert rel_l2(O.dst1(x), 1j * brute_dft(z)[1:n + 1]) < 1e-13
+
+
+def test_round_trip_sine():
+    f = rand_real((11, 6, 8), 21)
+    tt = (O.FFT, O.FFT, O.SINE)
+    g = O.backward(O.forward(f, tt), 8, tt)
+    assert rel_l2(g, O.scale(8, 6, 11, tt) * f) < 1e-13
+    assert O.scale(8, 6, 11, tt) == 8 * 6 * 24
+
+
 # --------------------------------------------------------------------------
 # Invariants
 # --------------------------------------------------------------------------
@@ -253,7 +299,7 @@ def test_linearity():
     shape = (6, 8, 10)
     f, g = rand_real(shape, 8), rand_real(shape, 9)
     a, b = 0.7, -2.5
-    for tt in ((O.FFT, O.FFT, O.FFT), (O.FFT, O.FFT, O.CHEB), (O.FFT, O.EMPTY, O.CHEB)):
+    for tt in ((O.FFT, O.FFT, O.FFT), (O.FFT, O.FFT, O.CHEB), (O.FFT, O.EMPTY, O.CHEB), (O.FFT, O.FFT, O.SINE)):
         lhs = O.forward(a * f + b * g, tt)
         rhs = a * O.forward(f, tt) + b * O.forward(g, tt)
         assert rel_l2(lhs, rhs) < 1e-14
@@ -313,6 +359,13 @@ def test_dct1_matches_scipy():
     assert rel_l2(O.dct1(x).real, sfft.dct(x, type=1)) < 1e-14
 
 
+def test_dst1_matches_scipy():
+    sfft = pytest.importorskip("scipy.fft")
+    for n in (1, 2, 17, 64):
+        x = rand_real((n,), 15 + n)
+        assert rel_l2(O.dst1(x).real, sfft.dst(x, type=1)) < 1e-14
+
+
 # --------------------------------------------------------------------------
 # The pins have teeth: plausible mistakes planted in copies of the oracle fail
 # --------------------------------------------------------------------------
@@ -323,6 +376,9 @@ MUTANTS = {
              "r[t] = (double)cosl(a) - (double)sign * (double)sinl(a) * I;"),
     # Nyquist weight of the c2r sum set to 2 like the interior bins
     "nyq_weight": ("if (nx % 2 == 0 && q == nx / 2) w = 1.0;", "if (0) w = 1.0;"),
+    # DST-I sample index off by one (sin(pi j (k+1)/(n+1)) instead of (j+1))
+    "dst_index": ("acc += 2.0 * k->sinv[((j + 1) * (q + 1)) % P] * line[j];",
+                  "acc += 2.0 * k->sinv[(j * (q + 1)) % P] * line[j];"),
     # DCT-I end point dropped
     "dct_end": ("cplx acc = line[0] + ((q % 2) ? -line[M] : line[M]);", "cplx acc = line[0];"),
     # recombination index off: transposed operand
@@ -349,12 +405,12 @@ def test_planted_mistakes(tmp_path, name):
     lib.p3o_forward.argtypes = [L, L, L, I, I, P, P, I]
     lib.p3o_backward.argtypes = [L, L, L, I, I, P, P, I]
     failures = 0
-    for shape, tz in (((8, 6, 10), O.FFT), ((9, 5, 6), O.CHEB)):
+    for shape, tz in (((8, 6, 10), O.FFT), ((9, 5, 6), O.CHEB), ((7, 5, 6), O.SINE)):
         nz, ny, nx = shape
         f = rand_real(shape, 16)
         F = np.zeros((nz, ny, nx // 2 + 1), complex)
         lib.p3o_forward(nx, ny, nz, O.FFT, tz, f.ctypes.data, F.ctypes.data, 1)
-        if rel_l2(F, brute_forward_3d(f, "fft" if tz == O.FFT else "cheb")) > 1e-12:
+        if rel_l2(F, brute_forward_3d(f, {O.FFT: "fft", O.CHEB: "cheb", O.SINE: "sine"}[tz])) > 1e-12:
             failures += 1
         G = rand_cplx(F.shape, 17)
         g = np.zeros(shape)
