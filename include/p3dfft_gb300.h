@@ -23,7 +23,9 @@
  *            kx < H; a CHEB third dimension replaces the Z sum with the DCT-I
  *            Y_n = x_0 + (-1)^n x_M + 2 sum_{j=1}^{M-1} x_j cos(pi j n / M), M = Nz-1
  *            (real and imaginary parts alike; Gauss-Lobatto points
- *            z_j = cos(pi j / M)); an EMPTY dimension is the identity.
+ *            z_j = cos(pi j / M)), a SINE third dimension the DST-I (the
+ *            inverse applies the same DST-I again: scale 2(Nz+1)); an EMPTY
+ *            dimension is the identity.
  *   inverse  the adjoint stages in reverse order with the + sign, the X stage
  *            being f[x] = Re sum_{k<H} w_k F[k] exp(+2 pi i k x / Nx) with
  *            w_0 = 1, w_{Nx/2} = 1 for even Nx, w_k = 2 otherwise (so the
@@ -37,8 +39,9 @@
  *
  * Execution: ftran / btran enqueue kernels on `stream` (a cudaStream_t; NULL
  * is the legacy default stream) and return without synchronising.  Inputs are
- * never written.  Out-of-place only: an output that overlaps the input or the
- * workspace is rejected.  A plan is immutable after creation (except for the
+ * never written (except in place, see P3_FLAG_PADDED_REAL).  An output that
+ * partly overlaps the input, or any buffer overlapping the workspace, is
+ * rejected.  A plan is immutable after creation (except for the
  * optional timing events) and may be used from several threads with distinct
  * workspaces.  No call throws, aborts or prints.
  */
@@ -68,11 +71,15 @@ typedef enum {
 /* Sect. 3.1: single and double precision. */
 typedef enum { P3_F32 = 0, P3_F64 = 1 } p3_precision;
 
-/* Sect. 3.1 / Sect. 5: Fourier, Chebyshev (DCT-I, third dimension only), empty. */
-typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2 } p3_ttype;
+/* Sect. 3.1 / Sect. 5: Fourier, Chebyshev (DCT-I, third dimension only),
+ * empty, and sine (DST-I of the Nz interior points of a Dirichlet grid,
+ * Y_k = 2 sum_j x_j sin(pi (j+1)(k+1)/(Nz+1)), third dimension only; the
+ * "sine" of Sect. 3.1's sine/cosine transforms). */
+typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2, P3_SINE = 3 } p3_ttype;
 
 /* Plan flags (p3_plan_create). */
 #define P3_FLAG_TC_SPLIT 1u
+#define P3_FLAG_PADDED_REAL 2u
 
 /* Table 1: storage order of the Z-pencil complex array. */
 typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
@@ -85,12 +92,20 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *   prec       P3_F32 or P3_F64: the type of the data and of the arithmetic.
  *   ttype      per-dimension transform; ttype[0] must be P3_FFT (the X
  *              real-to-complex stage defines the path), ttype[1] P3_FFT or
- *              P3_EMPTY, ttype[2] P3_FFT, P3_CHEB or P3_EMPTY.
+ *              P3_EMPTY, ttype[2] P3_FFT, P3_CHEB, P3_SINE or P3_EMPTY.
  *   out_layout storage order of the complex array (Table 1).
- *   flags      0, or P3_FLAG_TC_SPLIT: run the FP32 1024-point Y / Z stages
- *              on the tensor cores in split precision (each FP32 operand
- *              split into a TF32 head and tail, three products accumulated
- *              in FP32).  No effect on other stages or precisions.
+ *   flags      0 or an OR of
+ *              P3_FLAG_TC_SPLIT: run the FP32 1024-point Y / Z stages on the
+ *                tensor cores in split precision (each FP32 operand split
+ *                into a TF32 head and tail, three products accumulated in
+ *                FP32).  No effect on other stages or precisions.
+ *              P3_FLAG_PADDED_REAL (P3_LAYOUT_XYZ only, else
+ *                P3_ERR_UNSUPPORTED): real arrays have rows of 2H values
+ *                (f[Nz][Ny][2H], the last 2H - Nx of each row unused), the
+ *                size of the complex array, so ftran and btran may run in
+ *                place (in == out; Sect. 3.1 in-place transforms).  Neither
+ *                direction then needs a workspace; out of place the inverse
+ *                works in its output buffer and leaves the input untouched.
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.
@@ -110,7 +125,8 @@ p3_status p3_plan_destroy(p3_plan plan);
  * Sect. 3.2).  in_real: Nx*Ny*Nz reals; out_cplx: H*Ny*Nz complex in the
  * plan's layout; workspace: p3_plan_workspace_bytes() bytes (may be NULL
  * when that is 0).  Errors: P3_ERR_INVALID (NULL plan/in/out, misaligned or
- * overlapping buffers), P3_ERR_UNSUPPORTED (in == out), P3_ERR_WORKSPACE,
+ * partly overlapping buffers), P3_ERR_UNSUPPORTED (in == out without
+ * P3_FLAG_PADDED_REAL), P3_ERR_WORKSPACE,
  * P3_ERR_CUDA (launch failure; the stream state is then undefined).
  */
 p3_status p3_ftran_r2c(p3_plan plan, const void* in_real, void* out_cplx,

@@ -43,6 +43,7 @@ enum StageOp : int {
     OP_C2R_FULL = 4,  // odd Nx: weighted, zero-padded line, complex FFT, real part
     OP_DCT1 = 5,      // Chebyshev: even extension to 2M points, FFT, first M+1 bins
     OP_COPY = 6,      // empty transform (re-orientation only)
+    OP_DST1 = 7,      // sine: odd extension to 2(n+1) points, FFT, i times bins 1..n
 };
 
 // Everything one stage kernel launch needs (passed by value).

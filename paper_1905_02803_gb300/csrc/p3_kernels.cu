@@ -147,6 +147,19 @@ __device__ __forceinline__ C load_value(const StageArgs& a, long long base, int 
         v = X[base + (long long)src * es];
         break;
     }
+    case OP_DST1: {  // odd extension y = (0, x[0..n-1], 0, -x[n-1..0])
+        const C* X = static_cast<const C*>(a.src);
+        const int n = a.n_in;
+        if (e == 0 || e == n + 1) {
+            v = mk<C>((T)0, (T)0);
+        } else if (e <= n) {
+            v = X[base + (long long)(e - 1) * es];
+        } else {
+            const C u = X[base + (long long)(2 * n + 1 - e) * es];
+            v = mk<C>(-u.x, -u.y);
+        }
+        break;
+    }
     default: {  // OP_C2C, OP_COPY
         const C* X = static_cast<const C*>(a.src);
         v = X[base + (long long)e * es];
@@ -187,6 +200,11 @@ __device__ __forceinline__ void store_value(const StageArgs& a, const C* sl, int
     case OP_DCT1:
         static_cast<C*>(a.dst)[base + (long long)e * es] = result(a, sl, LDB, e);
         break;
+    case OP_DST1: {  // Y[e] = i Z[e + 1] (forward sign: Z[k] = -2i sum x_j sin(pi k (j+1)/(n+1)))
+        const C z = result(a, sl, LDB, e + 1);
+        static_cast<C*>(a.dst)[base + (long long)e * es] = mk<C>(-z.y, z.x);
+        break;
+    }
     case OP_C2R_HALF: {  // f[2j] = Re z[j], f[2j+1] = Im z[j]
         const C z = swp(result(a, sl, LDB, e));
         *reinterpret_cast<C*>(static_cast<T*>(a.dst) + base + 2 * (long long)e) = z;

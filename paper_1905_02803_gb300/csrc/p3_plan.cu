@@ -69,6 +69,7 @@ struct p3_plan_s {
     std::vector<Stage> st[2];
     size_t ws_bytes;
     double scale;
+    bool padded;  // real rows of 2H values (in-place capable, XYZ layout)
     void* events[8];
     bool timing;
     std::string desc;
@@ -295,6 +296,7 @@ const char* op_name(int op)
     case p3::OP_C2R_HALF: return "c2r_half";
     case p3::OP_C2R_FULL: return "c2r_full";
     case p3::OP_DCT1: return "dct1";
+    case p3::OP_DST1: return "dst1";
     default: return "copy";
     }
 }
@@ -354,19 +356,24 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
 {
     if (!out) return P3_ERR_INVALID;
     *out = NULL;
-    if (!ttype || nx < 1 || ny < 1 || nz < 1 || (flags & ~(unsigned)P3_FLAG_TC_SPLIT)) return P3_ERR_INVALID;
+    if (!ttype || nx < 1 || ny < 1 || nz < 1 || (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL)))
+        return P3_ERR_INVALID;
     if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
     if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
     for (int d = 0; d < 3; ++d)
-        if (ttype[d] != P3_FFT && ttype[d] != P3_CHEB && ttype[d] != P3_EMPTY) return P3_ERR_INVALID;
+        if (ttype[d] != P3_FFT && ttype[d] != P3_CHEB && ttype[d] != P3_EMPTY && ttype[d] != P3_SINE)
+            return P3_ERR_INVALID;
     if (ttype[0] != P3_FFT) return P3_ERR_UNSUPPORTED;
-    if (ttype[1] == P3_CHEB) return P3_ERR_UNSUPPORTED;
+    if (ttype[1] == P3_CHEB || ttype[1] == P3_SINE) return P3_ERR_UNSUPPORTED;
     if (ttype[2] == P3_CHEB && nz < 2) return P3_ERR_INVALID;
+    const bool padded = (flags & P3_FLAG_PADDED_REAL) != 0;
+    if (padded && out_layout != P3_LAYOUT_XYZ) return P3_ERR_UNSUPPORTED;
     // per-line length limits
     if (!smooth_or_small(nx % 2 == 0 ? nx / 2 : nx)) return P3_ERR_UNSUPPORTED;
     if (ttype[1] == P3_FFT && !smooth_or_small(ny)) return P3_ERR_UNSUPPORTED;
     if (ttype[2] == P3_FFT && !smooth_or_small(nz)) return P3_ERR_UNSUPPORTED;
     if (ttype[2] == P3_CHEB && !smooth_or_small(2 * (nz - 1))) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_SINE && !smooth_or_small(2 * (nz + 1))) return P3_ERR_UNSUPPORTED;
 
     p3_plan P = new (std::nothrow) p3_plan_s();
     if (!P) return P3_ERR_NOMEM;
@@ -374,18 +381,23 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     P->prec = prec;
     for (int d = 0; d < 3; ++d) P->tt[d] = ttype[d];
     P->layout = out_layout;
+    P->padded = padded;
     P->csize = prec == P3_F32 ? 8 : 16;
     P->dtab = NULL;
     P->timing = false;
     memset(P->events, 0, sizeof(P->events));
     const long long H = P->H, NY = ny, NZ = nz, NX = nx;
     const size_t e = P->csize / 2;
+    const long long RP = padded ? 2 * H : NX;             // real row pitch (elements)
     const double creal = (double)e * NX * NY * NZ;        // bytes of the real array
     const double ccplx = (double)P->csize * H * NY * NZ;  // bytes of the complex array
 
     P->scale = (double)nx;
     P->scale *= ttype[1] == P3_FFT ? (double)ny : 1.0;
-    P->scale *= ttype[2] == P3_FFT ? (double)nz : (ttype[2] == P3_CHEB ? 2.0 * (nz - 1) : 1.0);
+    P->scale *= ttype[2] == P3_FFT    ? (double)nz
+                : ttype[2] == P3_CHEB ? 2.0 * (nz - 1)
+                : ttype[2] == P3_SINE ? 2.0 * (nz + 1)
+                                      : 1.0;
 
     TableSet T;
     std::vector<Pending> pend[2];
@@ -441,7 +453,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         const bool half = nx % 2 == 0;
         const int nfft = half ? nx / 2 : nx;
         StageArgs a = base_args(half ? p3::OP_R2C_HALF : p3::OP_R2C_FULL, nx, (int)H, nfft, -1, NY * NZ,
-                                rows(NY * NZ, NX), rows(NY * NZ, H));
+                                rows(NY * NZ, RP), rows(NY * NZ, H));
         push(0, a, BUF_IN, zyx ? BUF_WS : BUF_OUT, "x_r2c", creal + ccplx, half ? nx : nx);
         const int work = zyx ? BUF_WS : BUF_OUT;
         if (ttype[1] == P3_FFT && ny > 1) {
@@ -455,38 +467,50 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         } else if (ttype[2] == P3_CHEB) {
             a = base_args(p3::OP_DCT1, nz, nz, 2 * (nz - 1), -1, H * NY, mapZxyz, zout);
             push(0, a, work, BUF_OUT, zyx ? "z_dct1_zyx" : "z_dct1", 2 * ccplx, 2 * (nz - 1));
+        } else if (ttype[2] == P3_SINE) {
+            a = base_args(p3::OP_DST1, nz, nz, 2 * (nz + 1), -1, H * NY, mapZxyz, zout);
+            push(0, a, work, BUF_OUT, zyx ? "z_dst1_zyx" : "z_dst1", 2 * ccplx, 2 * (nz + 1));
         } else if (zyx) {
             a = base_args(p3::OP_COPY, nz, nz, 1, -1, H * NY, mapZxyz, zout);
             push(0, a, work, BUF_OUT, "z_copy_zyx", 2 * ccplx, 1);
         }
     }
     // ---- inverse: Z, Y, X c2r -------------------------------------------
+    // The work buffer is the workspace, or with padded real rows the output
+    // itself (it holds H*Ny*Nz complex values), so the input stays untouched
+    // out of place and everything runs in place when in == out.
+    const int WORK = padded ? BUF_OUT : BUF_WS;
     {
         int cur = BUF_IN;
         const LineMap zin = zyx ? mapZzyx : mapZxyz;
         StageArgs a;
         if (ttype[2] == P3_FFT && nz > 1) {
             a = base_args(p3::OP_C2C, nz, nz, nz, +1, H * NY, zin, mapZxyz);
-            push(1, a, cur, BUF_WS, zyx ? "z_c2c_zyx_inv" : "z_c2c_inv", 2 * ccplx, nz);
-            cur = BUF_WS;
+            push(1, a, cur, WORK, zyx ? "z_c2c_zyx_inv" : "z_c2c_inv", 2 * ccplx, nz);
+            cur = WORK;
         } else if (ttype[2] == P3_CHEB) {
             a = base_args(p3::OP_DCT1, nz, nz, 2 * (nz - 1), +1, H * NY, zin, mapZxyz);
-            push(1, a, cur, BUF_WS, zyx ? "z_dct1_zyx_inv" : "z_dct1_inv", 2 * ccplx, 2 * (nz - 1));
-            cur = BUF_WS;
+            push(1, a, cur, WORK, zyx ? "z_dct1_zyx_inv" : "z_dct1_inv", 2 * ccplx, 2 * (nz - 1));
+            cur = WORK;
+        } else if (ttype[2] == P3_SINE) {
+            // DST-I is its own inverse up to 2(Nz+1): same sign both ways
+            a = base_args(p3::OP_DST1, nz, nz, 2 * (nz + 1), -1, H * NY, zin, mapZxyz);
+            push(1, a, cur, WORK, zyx ? "z_dst1_zyx_inv" : "z_dst1_inv", 2 * ccplx, 2 * (nz + 1));
+            cur = WORK;
         } else if (zyx) {
             a = base_args(p3::OP_COPY, nz, nz, 1, +1, H * NY, zin, mapZxyz);
-            push(1, a, cur, BUF_WS, "z_copy_zyx_inv", 2 * ccplx, 1);
-            cur = BUF_WS;
+            push(1, a, cur, WORK, "z_copy_zyx_inv", 2 * ccplx, 1);
+            cur = WORK;
         }
         if (ttype[1] == P3_FFT && ny > 1) {
             a = base_args(p3::OP_C2C, ny, ny, ny, +1, H * NZ, mapY, mapY);
-            push(1, a, cur, BUF_WS, "y_c2c_inv", 2 * ccplx, ny);
-            cur = BUF_WS;
+            push(1, a, cur, WORK, "y_c2c_inv", 2 * ccplx, ny);
+            cur = WORK;
         }
         const bool half = nx % 2 == 0;
         const int nfft = half ? nx / 2 : nx;
         a = base_args(half ? p3::OP_C2R_HALF : p3::OP_C2R_FULL, (int)H, half ? nfft : nx, nfft, +1, NY * NZ,
-                      rows(NY * NZ, H), rows(NY * NZ, NX));
+                      rows(NY * NZ, H), rows(NY * NZ, RP));
         push(1, a, cur, BUF_OUT, "x_c2r", creal + ccplx, nx);
     }
     if (rc != P3_OK) {
@@ -611,11 +635,12 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
 {
     if (!P || !in || !out) return P3_ERR_INVALID;
     if (!aligned16(in) || !aligned16(out) || (ws && !aligned16(ws))) return P3_ERR_INVALID;
-    if (in == out) return P3_ERR_UNSUPPORTED;
-    const size_t nreal = (size_t)P->nx * P->ny * P->nz * (P->csize / 2);
+    if (in == out && !P->padded) return P3_ERR_UNSUPPORTED;
+    const size_t rowr = P->padded ? 2 * (size_t)P->H : (size_t)P->nx;
+    const size_t nreal = rowr * P->ny * P->nz * (P->csize / 2);
     const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
     const size_t nin = dir == 0 ? nreal : ncplx, nout = dir == 0 ? ncplx : nreal;
-    if (overlap(in, nin, out, nout)) return P3_ERR_INVALID;
+    if (in != out && overlap(in, nin, out, nout)) return P3_ERR_INVALID;
     bool uses_ws = false;
     for (auto& s : P->st[dir])
         if (s.src == BUF_WS || s.dst == BUF_WS) uses_ws = true;

@@ -5,10 +5,13 @@
 
 namespace p3 {
 
-void* pow2_pick_f32(int kind, int N, bool inv, bool dct, bool pl);
-void* pow2_pick_f64(int kind, int N, bool inv, bool dct, bool pl);
-void pow2_shape_f32(int kind, int N, int* B, int* tpl, size_t* smem, int* pl);
-void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem, int* pl);
+void* pow2_pick_f32(int kind, int N, bool inv, int sym, bool pl);
+void* pow2_pick_f64(int kind, int N, bool inv, int sym, bool pl);
+void pow2_shape_f32(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
+void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
+
+// Column-kernel symmetry variant of a stage: 0 plain, 1 DCT-I, 2 DST-I.
+static int sym_of(const StageArgs& a) { return a.op == OP_DCT1 ? 1 : a.op == OP_DST1 ? 2 : 0; }
 
 namespace {
 bool is_pow2_in_range(int n) { return n >= 64 && n <= 4096 && (n & (n - 1)) == 0; }
@@ -31,7 +34,7 @@ static bool configure(StageArgs& a, size_t csize)
     if (!is_pow2_in_range(N)) return false;
     const bool f32 = csize == 8;
     int kind = 0;
-    if (a.op == OP_C2C || a.op == OP_DCT1) {
+    if (a.op == OP_C2C || a.op == OP_DCT1 || a.op == OP_DST1) {
         const bool in_adj = a.in.lstride == 1, out_adj = a.out.lstride == 1;
         const bool in_el = a.in.es == 1, out_el = a.out.es == 1;
         if (in_adj && out_adj && !in_el && !out_el) kind = KIND_COL_DD;
@@ -46,8 +49,9 @@ static bool configure(StageArgs& a, size_t csize)
     }
     int B = 1, tpl = 1, pl = 0;
     size_t smem = 0;
-    if (f32) pow2_shape_f32(kind, N, &B, &tpl, &smem, &pl);
-    else pow2_shape_f64(kind, N, &B, &tpl, &smem, &pl);
+    const bool allow_pl = a.op != OP_DST1;
+    if (f32) pow2_shape_f32(kind, N, allow_pl, &B, &tpl, &smem, &pl);
+    else pow2_shape_f64(kind, N, allow_pl, &B, &tpl, &smem, &pl);
     a.B = B;
     a.LDB = B;
     a.tpl = tpl;
@@ -57,8 +61,8 @@ static bool configure(StageArgs& a, size_t csize)
     a.persist = 0;
     if (pl) {
         // persistent grid: resident CTAs per SM times the SM count
-        void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, a.op == OP_DCT1, true)
-                       : pow2_pick_f64(kind, N, a.sign > 0, a.op == OP_DCT1, true);
+        void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, sym_of(a), true)
+                       : pow2_pick_f64(kind, N, a.sign > 0, sym_of(a), true);
         int dev = 0, sms = 0, per = 0;
         if (fn && cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
@@ -79,9 +83,9 @@ cudaError_t pow2_prepare()
         for (int kind = KIND_COL_DD; kind <= KIND_ROW_C2R; ++kind)
             for (int N = 64; N <= 4096; N *= 2)
                 for (int inv = 0; inv < 2; ++inv)
-                    for (int dct = 0; dct < 2; ++dct)
+                    for (int sym = 0; sym < 3; ++sym)
                         for (int pl = 0; pl < 2; ++pl) {
-                            void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, dct, pl) : pow2_pick_f64(kind, N, inv, dct, pl);
+                            void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, sym, pl) : pow2_pick_f64(kind, N, inv, sym, pl);
                             if (!fn) continue;
                             cudaError_t e =
                                 cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -92,8 +96,9 @@ cudaError_t pow2_prepare()
 
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
 {
-    const bool inv = a.sign > 0, dct = a.op == OP_DCT1, pl = a.persist > 0;
-    void* fn = f32 ? pow2_pick_f32(a.kern, a.nfft, inv, dct, pl) : pow2_pick_f64(a.kern, a.nfft, inv, dct, pl);
+    const bool inv = a.sign > 0, pl = a.persist > 0;
+    const int sym = sym_of(a);
+    void* fn = f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym, pl) : pow2_pick_f64(a.kern, a.nfft, inv, sym, pl);
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;
     long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;

@@ -189,11 +189,16 @@ template <> struct Vec4<float> { typedef float4 t; };
 // MODE 0: HBM -> regs ... regs -> HBM (both sides line-adjacent)
 // MODE 1: HBM -> regs ... smem -> HBM with lanes along elements (ZYX store)
 // MODE 2: HBM (lanes along elements) -> smem -> regs ... regs -> HBM (ZYX load)
-// INV: inverse sign (swp on load and store); DCT: Chebyshev even extension.
-template <typename T, int N, int E, int B, int MODE, bool INV, bool DCT>
+// INV: inverse sign (swp on load and store).
+// SYM 0: plain line; 1: Chebyshev even extension (DCT-I of M + 1 points);
+// 2: odd extension (DST-I of M - 1 points: element e reads 0 at e = 0, M,
+// x[e - 1] below M and -x[N - 1 - e] above; output k is i times bin k + 1).
+template <typename T, int N, int E, int B, int MODE, bool INV, int SYM>
 __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
     col_kernel(const __grid_constant__ StageArgs a)
 {
+    static_assert(SYM != 2 || !INV, "the sine transform always runs with the forward sign");
+    constexpr bool DCT = SYM == 1, DST = SYM == 2;
     typedef typename CxT<T>::t C;
     typedef P2<N, E> PL;
     constexpr int NP = PL::NPASS;
@@ -220,9 +225,16 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
             for (int r = 0; r < P0::R; ++r) {
                 const int K = P0::in_K(b, r);
                 const int e = t + K;
-                // even extension of a Chebyshev line: element e > M reads N - e
-                const long long off = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
-                C x = valid ? src[off] : zero;
+                C x;
+                if constexpr (DST) {
+                    const long long off = (long long)(e < M ? e - 1 : N - 1 - e) * es;
+                    x = (valid && e != 0 && e != M) ? src[off] : zero;
+                    if (e > M) x = mk<C>(-x.x, -x.y);
+                } else {
+                    // even extension of a Chebyshev line: element e > M reads N - e
+                    const long long off = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
+                    x = valid ? src[off] : zero;
+                }
                 v[b * P0::R + r] = INV ? swp(x) : x;
             }
     } else {
@@ -230,7 +242,12 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         long long Le;
         const bool ve = tile_line(a, B, le, &Le);
         const C* src = static_cast<const C*>(a.src) + (ve ? lbase(a.in, Le) : 0);
-        if constexpr (DCT || Ef::VEC == 1) {
+        if constexpr (DST) {
+            for (int c = Ef::chunk0(tid); c < N; c += Ef::STEP) {
+                C x = (ve && c != 0 && c != M) ? src[c < M ? c - 1 : N - 1 - c] : zero;
+                s[S::at(c, le)] = c > M ? mk<C>(-x.x, -x.y) : x;
+            }
+        } else if constexpr (DCT || Ef::VEC == 1) {
             for (int c = Ef::chunk0(tid); c < N; c += Ef::STEP) {
                 const int ee = DCT ? (c <= M ? c : N - c) : c;
                 C x = ve ? src[ee] : zero;
@@ -267,7 +284,11 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                 for (int r = 0; r < PLast::R; ++r) {
                     const int e = u + PLast::out_K(b, r);
                     const C x = v[b * PLast::R + r];
-                    if (!DCT || e <= M) dst[(long long)e * es] = INV ? swp(x) : x;
+                    if constexpr (DST) {
+                        if (e >= 1 && e < M) dst[(long long)(e - 1) * es] = mk<C>(-x.y, x.x);
+                    } else {
+                        if (!DCT || e <= M) dst[(long long)e * es] = INV ? swp(x) : x;
+                    }
                 }
         }
     } else {
@@ -285,7 +306,12 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         long long Le;
         if (tile_line(a, B, le, &Le)) {
             C* dst = static_cast<C*>(a.dst) + lbase(a.out, Le);
-            if constexpr (DCT || Ef::VEC == 1) {
+            if constexpr (DST) {
+                for (int c = Ef::chunk0(tid); c < M - 1; c += Ef::STEP) {
+                    const C x = s[S::at(c + 1, le)];
+                    dst[c] = mk<C>(-x.y, x.x);
+                }
+            } else if constexpr (DCT || Ef::VEC == 1) {
                 for (int c = Ef::chunk0(tid); c < (DCT ? M + 1 : N); c += Ef::STEP) {
                     const C x = s[S::at(c, le)];
                     dst[c] = INV ? swp(x) : x;
@@ -467,7 +493,8 @@ __global__ void __launch_bounds__(B * (N / E), 1) col_kernel_pl(const __grid_con
 }
 
 // ---------------------------------------------------------------------------
-// Row kernels: X stage, Nx = 2N real points per row, H = N + 1 bins.
+// Row kernels: X stage, Nx = 2N real points per row, H = N + 1 bins; row
+// L starts at L * lstride of its array (real rows may be padded).
 // OPR 0: r2c (forward), OPR 1: c2r (inverse).
 // ---------------------------------------------------------------------------
 template <int N, int E> struct RowSlot {
@@ -531,7 +558,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 
     if constexpr (OPR == 0) {
         // z[j] = f[2j] + i f[2j+1]
-        const C* src = reinterpret_cast<const C*>(static_cast<const T*>(a.src) + (valid ? L * (2LL * N) : 0));
+        const C* src = reinterpret_cast<const C*>(static_cast<const T*>(a.src) + (valid ? L * a.in.lstride : 0));
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
 #pragma unroll
@@ -539,7 +566,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     } else {
         // Z[k] = (F[k] + conj F[N-k]) + i (F[k] - conj F[N-k]) exp(+2 pi i k / 2N),
         // imaginary parts of F[0] and F[N] dropped; inverse via swp
-        const C* src = static_cast<const C*>(a.src) + (valid ? L * (long long)H : 0);
+        const C* src = static_cast<const C*>(a.src) + (valid ? L * a.in.lstride : 0);
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
 #pragma unroll
@@ -571,7 +598,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         }
         __syncthreads();
         if (valid) {
-            C* dst = static_cast<C*>(a.dst) + L * (long long)H;
+            C* dst = static_cast<C*>(a.dst) + L * a.out.lstride;
             for (int k = t; k <= N; k += TPL) {
                 const C zk = srow[S::at(k == N ? 0 : k)];
                 const C zm = cnj(srow[S::at(k == 0 ? 0 : N - k)]);
@@ -581,7 +608,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         }
     } else {
         if (valid) {
-            C* dst = reinterpret_cast<C*>(static_cast<T*>(a.dst) + L * (2LL * N));
+            C* dst = reinterpret_cast<C*>(static_cast<T*>(a.dst) + L * a.out.lstride);
             const int u = PLast::out_u(t);
 #pragma unroll
             for (int b = 0; b < PLast::BM; ++b)

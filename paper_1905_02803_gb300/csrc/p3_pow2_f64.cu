@@ -6,23 +6,25 @@ namespace p3 {
 namespace {
 using namespace pw;
 
-template <int N, int MODE, bool INV, bool DCT> void* col_fn()
+template <int N, int MODE, bool INV, int SYM> void* col_fn()
 {
-    return (void*)col_kernel<double, N, col_E<double>(N, MODE), col_B<double>(N), MODE, INV, DCT>;
+    return (void*)col_kernel<double, N, col_E<double>(N, MODE), col_B<double>(N), MODE, INV, SYM>;
 }
-template <int N, int MODE, bool INV, bool DCT> void* col_pl_fn()
+template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
 {
-    if constexpr (col_pipelined<double>(N, MODE))
-        return (void*)col_kernel_pl<double, N, col_pl_E<double>(N, MODE), col_B<double>(N), MODE, INV, DCT>;
+    if constexpr (SYM != 2 && col_pipelined<double>(N, MODE))
+        return (void*)col_kernel_pl<double, N, col_pl_E<double>(N, MODE), col_B<double>(N), MODE, INV, SYM == 1>;
     else
         return nullptr;
 }
 template <int N, int OPR> void* row_fn() { return (void*)row_kernel<double, N, row_E<double>(N), row_B<double>(N), OPR>; }
 
+// sym: 0 plain, 1 Chebyshev (DCT-I), 2 sine (DST-I, forward sign only)
 #define P3_COL_PICK(FN, MODE) \
-    (inv ? (dct ? FN<N, MODE, true, true>() : FN<N, MODE, true, false>()) \
-         : (dct ? FN<N, MODE, false, true>() : FN<N, MODE, false, false>()))
-template <int N> void* pick_n(int kind, bool inv, bool dct, bool pl)
+    (sym == 2 ? (inv ? (void*)nullptr : FN<N, MODE, false, 2>()) \
+     : inv ? (sym ? FN<N, MODE, true, 1>() : FN<N, MODE, true, 0>()) \
+           : (sym ? FN<N, MODE, false, 1>() : FN<N, MODE, false, 0>()))
+template <int N> void* pick_n(int kind, bool inv, int sym, bool pl)
 {
     switch (kind) {
     case KIND_COL_DD: return pl ? P3_COL_PICK(col_pl_fn, 0) : P3_COL_PICK(col_fn, 0);
@@ -36,21 +38,21 @@ template <int N> void* pick_n(int kind, bool inv, bool dct, bool pl)
 #undef P3_COL_PICK
 }  // namespace
 
-void* pow2_pick_f64(int kind, int N, bool inv, bool dct, bool pl)
+void* pow2_pick_f64(int kind, int N, bool inv, int sym, bool pl)
 {
     switch (N) {
-    case 64: return pick_n<64>(kind, inv, dct, pl);
-    case 128: return pick_n<128>(kind, inv, dct, pl);
-    case 256: return pick_n<256>(kind, inv, dct, pl);
-    case 512: return pick_n<512>(kind, inv, dct, pl);
-    case 1024: return pick_n<1024>(kind, inv, dct, pl);
-    case 2048: return pick_n<2048>(kind, inv, dct, pl);
-    case 4096: return pick_n<4096>(kind, inv, dct, pl);
+    case 64: return pick_n<64>(kind, inv, sym, pl);
+    case 128: return pick_n<128>(kind, inv, sym, pl);
+    case 256: return pick_n<256>(kind, inv, sym, pl);
+    case 512: return pick_n<512>(kind, inv, sym, pl);
+    case 1024: return pick_n<1024>(kind, inv, sym, pl);
+    case 2048: return pick_n<2048>(kind, inv, sym, pl);
+    case 4096: return pick_n<4096>(kind, inv, sym, pl);
     default: return nullptr;
     }
 }
 
-void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem, int* pl)
+void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl)
 {
     using namespace pw;
     *pl = 0;
@@ -63,7 +65,7 @@ void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem, int* pl)
         const int mode = kind == KIND_COL_SD ? 2 : kind == KIND_COL_DS ? 1 : 0;
         *B = col_B<double>(N);
         const size_t slots = (size_t)(cpad_c(N - 1) + 1) * (size_t)(*B);
-        if (col_pipelined<double>(N, mode)) {
+        if (allow_pl && col_pipelined<double>(N, mode)) {
             *pl = 1;
             *tpl = N / col_pl_E<double>(N, mode);
             *smem = 2 * slots * sizeof(double) * 2;

@@ -16,9 +16,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libp3dfft_gb300.so")
 
 P3_OK, P3_ERR_INVALID, P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA, P3_ERR_TIMEOUT, P3_ERR_WORKSPACE = range(7)
 P3_F32, P3_F64 = 0, 1
-P3_FFT, P3_CHEB, P3_EMPTY = 0, 1, 2
+P3_FFT, P3_CHEB, P3_EMPTY, P3_SINE = 0, 1, 2, 3
 P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
 P3_FLAG_TC_SPLIT = 1
+P3_FLAG_PADDED_REAL = 2
 
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
@@ -162,7 +163,7 @@ def p3_plan_launches(plan, direction: int) -> int:
 # torch-facing wrapper
 # ---------------------------------------------------------------------------
 
-_TT = {"fft": P3_FFT, "cheb": P3_CHEB, "empty": P3_EMPTY}
+_TT = {"fft": P3_FFT, "cheb": P3_CHEB, "empty": P3_EMPTY, "sine": P3_SINE}
 _LAYOUT = {"zyx": P3_LAYOUT_ZYX, "xyz": P3_LAYOUT_XYZ}
 
 
@@ -186,6 +187,8 @@ class Plan:
                                             [_TT[t] for t in self.ttypes], _LAYOUT[layout], flags)
         self.real_dtype = torch.float32 if precision == "f32" else torch.float64
         self.complex_dtype = torch.complex64 if precision == "f32" else torch.complex128
+        self.flags = int(flags)
+        self.padded = bool(self.flags & P3_FLAG_PADDED_REAL)
         self.ws_bytes = p3_plan_workspace_bytes(self.handle)
         self.scale = p3_plan_scale(self.handle)
         self._ws = None
@@ -198,7 +201,8 @@ class Plan:
 
     @property
     def real_shape(self):
-        return (self.nz, self.ny, self.nx)
+        """(nz, ny, nx), or (nz, ny, 2H) with padded real rows."""
+        return (self.nz, self.ny, 2 * self.H if self.padded else self.nx)
 
     @property
     def complex_shape(self):
@@ -239,6 +243,14 @@ class Plan:
         p3_ftran_r2c(self.handle, x.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
                      self._stream(stream))
         return out
+
+    def complex_view(self, x):
+        """The complex array sharing storage with a padded real array (in place)."""
+        return self.torch.view_as_complex(x.view(self.nz, self.ny, self.H, 2))
+
+    def real_view(self, X):
+        """The padded real array sharing storage with a complex array (in place)."""
+        return self.torch.view_as_real(X).view(self.nz, self.ny, 2 * self.H)
 
     def backward(self, X, out=None, ws=None, stream=None):
         self._check_tensor(X, self.complex_shape, self.complex_dtype, "input")

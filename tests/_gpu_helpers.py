@@ -6,7 +6,7 @@ from paper_1905_02803_gb300 import inputs
 
 TOL = {"f32": 2e-6, "f64": 1e-13}
 TOL_TC = 5e-6  # tensor-core split-precision stages (FP32 data)
-TT = {"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY}
+TT = {"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY, "sine": O.SINE}
 
 
 def rel_l2(got, ref):

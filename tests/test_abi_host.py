@@ -61,11 +61,15 @@ FFT3 = (P.P3_FFT, P.P3_FFT, P.P3_FFT)
     ((8, -1, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, 7, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, FFT3, 5, 0), P.P3_ERR_INVALID),
-    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 2), P.P3_ERR_INVALID),
+    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 4), P.P3_ERR_INVALID),
+    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, P.P3_FLAG_PADDED_REAL), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_FFT, 9), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 1, P.P3_F64, (P.P3_FFT, P.P3_FFT, P.P3_CHEB), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, (P.P3_EMPTY, P.P3_FFT, P.P3_FFT), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_CHEB, P.P3_FFT), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_SINE, P.P3_FFT), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_FFT, 4), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
+    ((8, 8, 2047 + 2048, P.P3_F32, (P.P3_FFT, P.P3_FFT, P.P3_SINE), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
     ((8, 8192, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 2053, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),   # prime > 2048
     ((2 * 4099, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),

@@ -3,7 +3,8 @@
 Tolerances: relative L2 <= 1e-13 for FP64 and <= 2e-6 for FP32.  Sizes span
 several CTA tiles with ragged tails, odd X lengths (no Nyquist bin), mixed
 radices 2/3/5/7, Bluestein lengths, degenerate extents of 1 and 2, the
-Chebyshev and empty third-dimension transforms, and both Z-pencil layouts.
+Chebyshev, sine and empty third-dimension transforms, and both Z-pencil
+layouts.
 """
 import numpy as np
 import pytest
@@ -62,7 +63,8 @@ def test_bluestein_lengths(shape, prec):
 
 
 @pytest.mark.parametrize("ttypes", [("fft", "fft", "cheb"), ("fft", "empty", "cheb"), ("fft", "empty", "empty"),
-                                    ("fft", "fft", "empty"), ("fft", "empty", "fft")])
+                                    ("fft", "fft", "empty"), ("fft", "empty", "fft"), ("fft", "fft", "sine"),
+                                    ("fft", "empty", "sine")])
 @pytest.mark.parametrize("layout", ["zyx", "xyz"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_transform_types(ttypes, layout, prec):
@@ -155,3 +157,34 @@ def test_tc_split_parity(shape, layout):
     ef, eb, plan = check_case(nx, ny, nz, "f32", layout=layout, seed=11, flags=P.P3_FLAG_TC_SPLIT)
     assert "tc_split_col" in plan.describe()
     assert ef <= TOL_TC and eb <= TOL_TC, (ef, eb)
+
+
+@pytest.mark.parametrize("nz", [1, 3, 9, 31, 63, 127, 511, 1023, 2047, 100])
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sine_third_dimension(nz, layout, prec):
+    """DST-I in Z: odd extension to 2(Nz+1) points; Nz = 2^k - 1 runs the
+    power-of-two column kernels (sine variant), others the generic kernel
+    (Nz = 100: 202 = 2 * 101 is a Bluestein length)."""
+    nx, ny = (24, 6) if nz >= 1023 else (34, 10)
+    ef, eb, plan = check_case(nx, ny, nz, prec, ttypes=("fft", "fft", "sine"), layout=layout, seed=nz)
+    assert ef <= TOL[prec] and eb <= TOL[prec], (ef, eb)
+    assert "dst1" in plan.describe()
+    if nz in (63, 127, 511, 1023, 2047):
+        assert "pow2_col" in plan.describe()
+    assert plan.scale == nx * ny * 2 * (nz + 1)
+
+
+def test_sine_mode_delta_on_gpu():
+    """f = sin(pi m (z+1)/(Nz+1)): the forward is Nx Ny (Nz+1) at
+    (kx, ky, kz) = (0, 0, m-1) and zero elsewhere."""
+    import torch
+    from paper_1905_02803_gb300.p3dfft import Plan
+    nx, ny, nz, m = 8, 4, 255, 5
+    plan = Plan(nx, ny, nz, precision="f64", ttypes=("fft", "fft", "sine"), layout="xyz")
+    zz = np.arange(nz)
+    f = np.broadcast_to(np.sin(np.pi * m * (zz + 1) / (nz + 1))[:, None, None], (nz, ny, nx)).copy()
+    X = plan.forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    expect = np.zeros_like(X)
+    expect[m - 1, 0, 0] = nx * ny * (nz + 1)
+    assert np.abs(X - expect).max() < 1e-9 * nx * ny * (nz + 1)
