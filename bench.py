@@ -234,7 +234,8 @@ def main():
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core split-precision comparison")
     ap.add_argument("--report", action="store_true",
                     help="measure every benchmark configuration (one JSON line each) instead of the 1024^3 line")
-    ap.add_argument("--report-only", default="", help="with --report: only the named config (batch64)")
+    ap.add_argument("--report-only", default="",
+                    help="with --report: only these comma-separated configs (names in REPORT_CONFIGS, or batch64)")
     ap.add_argument("--grid", default="1024",
                     help="grid edge N, or NX,NY,NZ (1024 is the benchmark workload; others are for profiling)")
     args = ap.parse_args()
@@ -450,10 +451,12 @@ REPORT_CONFIGS = [
     ("1024cube_f32", (1024, 1024, 1024), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
     ("2048cube_f32", (2048, 2048, 2048), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
     ("channel_480x360x257_f64", (480, 360, 257), "f64", ("fft", "fft", "cheb"), "zyx", "channel"),
+    ("sine_512x512x255_f32", (512, 512, 255), "f32", ("fft", "fft", "sine"), "zyx", "turbulence"),
+    ("inplace_512cube_f32_xyz", (512, 512, 512), "f32", ("fft", "fft", "fft"), "xyz", "turbulence", "inplace"),
 ]
 
 
-def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
+def _report_one(name, dims, prec, ttypes, layout, kind, mode="", *, steps, warmup):
     import numpy as np
     import torch
 
@@ -462,7 +465,9 @@ def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
     from paper_1905_02803_gb300 import p3dfft as P
 
     nx, ny, nz = dims
-    plan = P.Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout)
+    inplace = mode == "inplace"
+    plan = P.Plan(nx, ny, nz, precision=prec, ttypes=ttypes, layout=layout,
+                  flags=P.P3_FLAG_PADDED_REAL if inplace else 0)
     npdt = np.float32 if prec == "f32" else np.float64
     if kind == "config1":
         x = torch.from_numpy(inputs.config1_field(nx, 0)[0]).to("cuda", plan.real_dtype)
@@ -470,29 +475,51 @@ def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
         x = inputs.channel_field(nx, ny, nz, seed=0, dtype=npdt, device=plan.device)
     else:
         x = inputs.turbulence_field((nz, ny, nx), seed=0, dtype=npdt, device=plan.device)
-    X = plan.empty_complex()
-    y = plan.empty_real()
-    ws = plan.workspace()
-    for _ in range(warmup):
-        plan.forward(x, X, ws)
-        plan.backward(X, y, ws)
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(steps):
-        plan.forward(x, X, ws)
-        plan.backward(X, y, ws)
-    t1.record()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
+    if inplace:
+        # one padded buffer [nz][ny][2H]: forward and inverse both run with
+        # in == out; it is refilled from x outside each timed pair
+        buf = torch.zeros(plan.real_shape, dtype=plan.real_dtype, device=plan.device)
+        X = plan.complex_view(buf)
+        ws = None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(warmup + steps):
+            buf[..., :nx].copy_(x)
+            if i >= warmup:
+                ev[i - warmup][0].record()
+            plan.forward(buf, X)
+            plan.backward(X, buf)
+            if i >= warmup:
+                ev[i - warmup][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        y = buf[..., :nx]
+        buf2 = torch.zeros_like(buf)
+        buf2[..., :nx].copy_(x)
+        X = plan.forward(buf2)  # the forward result, for parity below
+    else:
+        X = plan.empty_complex()
+        y = plan.empty_real()
+        ws = plan.workspace()
+        for _ in range(warmup):
+            plan.forward(x, X, ws)
+            plan.backward(X, y, ws)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(steps):
+            plan.forward(x, X, ws)
+            plan.backward(X, y, ws)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
     e = 4 if prec == "f32" else 8
     pair_bytes = sum(stage_model_bytes(nx, ny, nz, e))
     peak, _ = peaks()
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
     N = nx * ny * nz
     gflops = 2 * 5 * N * math.log2(N) / (ms * 1e-3) / 1e9
-    tt = tuple({"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY}[t] for t in ttypes)
+    tt = tuple({"fft": O.FFT, "cheb": O.CHEB, "empty": O.EMPTY, "sine": O.SINE}[t] for t in ttypes)
     # parity: full oracle where it fits, else sampled lines (as the full-size tests)
     t_or = None
     if N <= 64 * 1024 * 1024:
@@ -506,6 +533,7 @@ def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
         err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         err_kind = "full rel-L2 vs oracle"
     else:
+        assert ttypes == ("fft", "fft", "fft"), "sampled-line parity covers the Fourier third dimension"
         pairs = [(0, 0), (1, 0), (3, 7), (ny // 2, nz - 1)]
         ps = O.PhaseSum(nx, ny, nz, [p[0] for p in pairs], [p[1] for p in pairs], -1)
         e_host = 0.0
@@ -529,6 +557,7 @@ def _report_one(name, dims, prec, ttypes, layout, kind, steps, warmup):
         den += (torch.linalg.vector_norm(xd) ** 2).item()
     rt = math.sqrt(num / den)
     return {"config": name, "grid": list(dims), "precision": prec, "ttypes": list(ttypes), "layout": layout,
+            "in_place": inplace,
             "ms": round(ms, 4), "gflops": round(gflops, 1), "stage_model_bytes": pair_bytes,
             "hbm_roofline_ms": round(roof_ms, 4), "hbm_roofline_frac": round(roof_ms / ms, 4),
             "rel_l2": err, "rel_l2_kind": err_kind, "round_trip_rel_l2": rt,
@@ -600,15 +629,16 @@ def _report_batch(steps, warmup):
 def run_report(args):
     import torch
     torch.cuda.set_device(0)
-    if args.report_only:
-        print(json.dumps(_report_batch(10, 2)), flush=True)
-        return
+    only = set(filter(None, args.report_only.split(",")))
     for c in REPORT_CONFIGS:
+        if only and c[0] not in only:
+            continue
         steps = 3 if c[1][0] >= 2048 else 20
         r = _report_one(*c, steps=steps, warmup=3)
         print(json.dumps(r), flush=True)
         torch.cuda.empty_cache()
-    print(json.dumps(_report_batch(10, 2)), flush=True)
+    if not only or "batch64" in only:
+        print(json.dumps(_report_batch(10, 2)), flush=True)
 
 
 if __name__ == "__main__":

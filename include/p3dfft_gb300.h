@@ -65,7 +65,8 @@ typedef enum {
     P3_ERR_NOMEM = 3,       /* host or device allocation at plan creation failed */
     P3_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
     P3_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    P3_ERR_WORKSPACE = 6    /* workspace required but NULL */
+    P3_ERR_WORKSPACE = 6,   /* workspace required but NULL */
+    P3_ERR_HOOK = 7         /* the user Z hook returned non-zero */
 } p3_status;
 
 /* Sect. 3.1: single and double precision. */
@@ -149,7 +150,8 @@ p3_status p3_plan_get_dims(p3_plan plan, int in_dims[3], int out_dims[3]);
 p3_status p3_plan_workspace_bytes(p3_plan plan, size_t* bytes);
 
 /* Round-trip factor: btran(ftran(f)) = scale * f, the product over the
-   dimensions of n (FFT), 2(n-1) (CHEB) or 1 (EMPTY) (Sect. 4.1). */
+   dimensions of n (FFT), 2(n-1) (CHEB), 2(n+1) (SINE) or 1 (EMPTY)
+   (Sect. 4.1); a Z hook's own factor is not included. */
 p3_status p3_plan_scale(p3_plan plan, double* scale);
 
 /*
@@ -169,8 +171,43 @@ p3_status p3_plan_set_stage_events(p3_plan plan, void* const* events, int n_even
  */
 p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len);
 
-/* Number of kernel launches one ftran (dir = 0) or btran (dir = 1) makes. */
+/* Number of kernel launches one ftran (dir = 0) or btran (dir = 1) makes
+   (with the Z hook set, if one is). */
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
+
+/*
+ * p3_z_hook -- a user transform in place of an EMPTY third dimension
+ * (Sect. 3.1 and Sect. 5: the empty transform leaves the third dimension to a
+ * transform of the user's own choice).  Called on the host, from inside
+ * ftran / btran, with:
+ *   data         device array of complex values (the plan's precision);
+ *   n            Nz, points per Z line;
+ *   nlines       H * Ny Z lines;
+ *   line_stride, elem_stride   element j of line L is
+ *                data[L * line_stride + j * elem_stride] (in complex
+ *                elements): ZYX forward output (Nz, 1), otherwise XYZ order
+ *                (1, H * Ny);
+ *   dir          0 forward, 1 inverse;
+ *   stream       the stream the caller passed to ftran / btran: the hook
+ *                must enqueue its work on it (or synchronise with it) and
+ *                may not block on later work of this call.
+ * It transforms the lines in place and returns 0, or non-zero to stop the
+ * call, which then returns P3_ERR_HOOK (stages already enqueued still run).
+ * Forward, it runs on the output after the last stage; inverse, on a copy of
+ * the input in the work buffer (workspace, or the output with
+ * P3_FLAG_PADDED_REAL), before the inverse Y and X stages; the input is not
+ * modified.
+ */
+typedef int (*p3_z_hook)(void* data, int n, long long nlines, long long line_stride, long long elem_stride,
+                         int dir, void* stream, void* user);
+
+/*
+ * Sets (fn != NULL) or clears (fn == NULL) the plan's Z hook; user is passed
+ * back to fn unchanged.  P3_ERR_INVALID for a NULL plan or a plan whose
+ * ttype[2] is not P3_EMPTY.  The workspace size already covers the hook
+ * mode.  Not thread-safe against concurrent ftran / btran on the same plan.
+ */
+p3_status p3_plan_set_z_hook(p3_plan plan, p3_z_hook fn, void* user);
 
 /*
  * p3_ftran_r2c_noalloc -- the forward transform of p3_ftran_r2c, but with the

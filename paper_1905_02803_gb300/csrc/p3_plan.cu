@@ -66,7 +66,11 @@ struct p3_plan_s {
     int device;
     size_t csize;  // bytes per complex element
     void* dtab;
-    std::vector<Stage> st[2];
+    // st[0] forward, st[1] inverse, st[2] the inverse used while a Z hook is
+    // set (EMPTY third dimension: a Z copy into the work buffer comes first)
+    std::vector<Stage> st[3];
+    p3_z_hook hook;
+    void* hook_user;
     size_t ws_bytes;
     double scale;
     bool padded;  // real rows of 2H values (in-place capable, XYZ layout)
@@ -345,6 +349,7 @@ const char* p3_status_string(p3_status s)
     case P3_ERR_CUDA: return "CUDA error";
     case P3_ERR_TIMEOUT: return "device wait timed out";
     case P3_ERR_WORKSPACE: return "workspace required";
+    case P3_ERR_HOOK: return "user Z hook failed";
     default: return "unknown status";
     }
 }
@@ -384,6 +389,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     P->padded = padded;
     P->csize = prec == P3_F32 ? 8 : 16;
     P->dtab = NULL;
+    P->hook = NULL;
+    P->hook_user = NULL;
     P->timing = false;
     memset(P->events, 0, sizeof(P->events));
     const long long H = P->H, NY = ny, NZ = nz, NX = nx;
@@ -400,7 +407,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
                                       : 1.0;
 
     TableSet T;
-    std::vector<Pending> pend[2];
+    std::vector<Pending> pend[3];
     p3_status rc = P3_OK;
 
     const LineMap mapY = LineMap{H, NY * H, 1, H};
@@ -513,12 +520,29 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
                       rows(NY * NZ, H), rows(NY * NZ, RP));
         push(1, a, cur, BUF_OUT, "x_c2r", creal + ccplx, nx);
     }
+    // ---- inverse with a user Z hook (EMPTY third dimension) ---------------
+    // The hook runs on a copy of the input in the work buffer (XYZ order),
+    // so the input stays untouched; then the inverse Y and X stages.
+    if (ttype[2] == P3_EMPTY) {
+        const LineMap zin = zyx ? mapZzyx : mapZxyz;
+        StageArgs a = base_args(p3::OP_COPY, nz, nz, 1, +1, H * NY, zin, mapZxyz);
+        push(2, a, BUF_IN, WORK, zyx ? "z_copy_zyx_inv" : "z_copy_inv", 2 * ccplx, 1);
+        if (ttype[1] == P3_FFT && ny > 1) {
+            a = base_args(p3::OP_C2C, ny, ny, ny, +1, H * NZ, mapY, mapY);
+            push(2, a, WORK, WORK, "y_c2c_inv", 2 * ccplx, ny);
+        }
+        const bool half = nx % 2 == 0;
+        const int nfft = half ? nx / 2 : nx;
+        a = base_args(half ? p3::OP_C2R_HALF : p3::OP_C2R_FULL, (int)H, half ? nfft : nx, nfft, +1, NY * NZ,
+                      rows(NY * NZ, H), rows(NY * NZ, RP));
+        push(2, a, WORK, BUF_OUT, "x_c2r", creal + ccplx, nx);
+    }
     if (rc != P3_OK) {
         delete P;
         return rc;
     }
     bool need_ws = false;
-    for (int d = 0; d < 2; ++d)
+    for (int d = 0; d < 3; ++d)
         for (auto& s : P->st[d])
             if (s.src == BUF_WS || s.dst == BUF_WS) need_ws = true;
     P->ws_bytes = need_ws ? (size_t)P->csize * (size_t)H * (size_t)NY * (size_t)NZ : 0;
@@ -563,7 +587,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     auto resolve = [&](size_t off) -> const void* {
         return off ? (const void*)((const unsigned char*)P->dtab + (off - 1) * P->csize) : NULL;
     };
-    for (int d = 0; d < 2; ++d) {
+    for (int d = 0; d < 3; ++d) {
         for (size_t i = 0; i < P->st[d].size(); ++i) {
             StageArgs& a = P->st[d][i].a;
             const Pending& pd = pend[d][i];
@@ -612,6 +636,13 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             P->desc += line;
         }
     }
+    if (!P->st[2].empty()) {
+        std::string names;
+        for (auto& s : P->st[2]) names += (names.empty() ? "" : ",") + std::string(s.name);
+        snprintf(line, sizeof(line), "z_hook fwd: after %s; bwd: after %s, then %s\n",
+                 P->st[0].empty() ? "-" : P->st[0].back().name, P->st[2][0].name, names.c_str());
+        P->desc += line;
+    }
     *out = P;
     return P3_OK;
 }
@@ -631,6 +662,15 @@ p3_status p3_plan_destroy(p3_plan plan)
     return P3_OK;
 }
 
+// The Z lines of the array the hook sees: ZYX output, Z contiguous; XYZ
+// (forward output or the inverse work copy), Z strided by H * Ny.
+static int call_hook(p3_plan P, int dir, void* data, void* stream)
+{
+    const long long H = P->H, NY = P->ny, NZ = P->nz;
+    const bool zyx = dir == 0 && P->layout == P3_LAYOUT_ZYX;
+    return P->hook(data, P->nz, H * NY, zyx ? NZ : 1, zyx ? 1 : H * NY, dir, stream, P->hook_user);
+}
+
 static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, void* stream)
 {
     if (!P || !in || !out) return P3_ERR_INVALID;
@@ -641,8 +681,14 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
     const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
     const size_t nin = dir == 0 ? nreal : ncplx, nout = dir == 0 ? ncplx : nreal;
     if (in != out && overlap(in, nin, out, nout)) return P3_ERR_INVALID;
+    // a Z hook replaces the empty third-dimension transform: forward, it
+    // runs after the last stage; inverse, after the copy of the input into
+    // the work buffer that starts the hook-mode stage list
+    const p3_z_hook hook = P->hook;
+    const std::vector<Stage>& stages = (dir == 1 && hook) ? P->st[2] : P->st[dir];
+    const size_t hook_after = hook ? (dir == 0 ? stages.size() : 1) : 0;
     bool uses_ws = false;
-    for (auto& s : P->st[dir])
+    for (auto& s : stages)
         if (s.src == BUF_WS || s.dst == BUF_WS) uses_ws = true;
     if (uses_ws) {
         if (!ws) return P3_ERR_WORKSPACE;
@@ -659,15 +705,17 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
     cudaEvent_t* ev = P->timing ? (cudaEvent_t*)&P->events[dir * 4] : NULL;
     if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return P3_ERR_CUDA;
     int i = 0;
-    for (auto& st : P->st[dir]) {
+    for (auto& st : stages) {
         StageArgs a = st.a;
         a.src = bufs[st.src];
         a.dst = bufs[st.dst];
         const cudaError_t e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
         if (e != cudaSuccess) return P3_ERR_CUDA;
         ++i;
+        if (hook && (size_t)i == hook_after && call_hook(P, dir, a.dst, stream) != 0) return P3_ERR_HOOK;
         if (ev && i <= 3 && cudaEventRecord(ev[i], s) != cudaSuccess) return P3_ERR_CUDA;
     }
+    if (hook && stages.empty() && call_hook(P, dir, out, stream) != 0) return P3_ERR_HOOK;
     if (ev)
         for (int k = i + 1; k <= 3; ++k)
             if (cudaEventRecord(ev[k], s) != cudaSuccess) return P3_ERR_CUDA;
@@ -739,7 +787,16 @@ p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len)
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches)
 {
     if (!plan || !launches || (dir != 0 && dir != 1)) return P3_ERR_INVALID;
-    *launches = (int)plan->st[dir].size();
+    *launches = (int)plan->st[dir == 1 && plan->hook ? 2 : dir].size();
+    return P3_OK;
+}
+
+p3_status p3_plan_set_z_hook(p3_plan plan, p3_z_hook fn, void* user)
+{
+    if (!plan) return P3_ERR_INVALID;
+    if (plan->tt[2] != P3_EMPTY) return P3_ERR_INVALID;
+    plan->hook = fn;
+    plan->hook_user = fn ? user : NULL;
     return P3_OK;
 }
 

@@ -14,7 +14,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libp3dfft_gb300.so")
 
-P3_OK, P3_ERR_INVALID, P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA, P3_ERR_TIMEOUT, P3_ERR_WORKSPACE = range(7)
+(P3_OK, P3_ERR_INVALID, P3_ERR_UNSUPPORTED, P3_ERR_NOMEM, P3_ERR_CUDA, P3_ERR_TIMEOUT, P3_ERR_WORKSPACE,
+ P3_ERR_HOOK) = range(8)
 P3_F32, P3_F64 = 0, 1
 P3_FFT, P3_CHEB, P3_EMPTY, P3_SINE = 0, 1, 2, 3
 P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
@@ -24,7 +25,12 @@ P3_FLAG_PADDED_REAL = 2
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
-           "p3_plan_launches", "p3_status_string", "p3_version")
+           "p3_plan_launches", "p3_plan_set_z_hook", "p3_status_string", "p3_version")
+
+# int hook(void* data, int n, long long nlines, long long line_stride, long long elem_stride,
+#          int dir, void* stream, void* user)
+Z_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                          ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 
 _lib = None
 
@@ -56,6 +62,7 @@ def load():
     lib.p3_plan_set_stage_events.argtypes = [P, ctypes.POINTER(P), I]
     lib.p3_plan_describe.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     lib.p3_plan_launches.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.p3_plan_set_z_hook.argtypes = [P, Z_HOOK, P]
     lib.p3_status_string.argtypes = [I]
     lib.p3_status_string.restype = ctypes.c_char_p
     lib.p3_version.argtypes = []
@@ -110,6 +117,14 @@ def p3_btran_c2r(plan, in_ptr, out_ptr, ws_ptr, stream, check=True):
 
 # Bytes of the library's built-in scratch array (include/p3dfft_gb300.h).
 P3_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def p3_plan_set_z_hook(plan, hook, user=None, check=True):
+    """hook: a Z_HOOK instance (keep a reference while it is set) or None."""
+    st = load().p3_plan_set_z_hook(plan, hook if hook is not None else Z_HOOK(), user)
+    if check:
+        _check(st, "p3_plan_set_z_hook")
+    return st
 
 
 def p3_ftran_r2c_noalloc(plan, in_ptr, out_ptr, stream, check=True):
@@ -192,6 +207,9 @@ class Plan:
         self.ws_bytes = p3_plan_workspace_bytes(self.handle)
         self.scale = p3_plan_scale(self.handle)
         self._ws = None
+        self._hook = None       # (python function, ctypes callback) while a Z hook is set
+        self._bufs = {}         # device pointer -> tensor, for the current call
+        self._hook_error = None
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -224,6 +242,47 @@ class Plan:
     def describe(self) -> str:
         return p3_plan_describe(self.handle)
 
+    def set_z_hook(self, fn):
+        """Run fn(lines, direction) in place of the EMPTY third-dimension
+        transform: lines is a strided complex view [H*Ny, Nz] of the device
+        data (one row per Z line) that fn transforms in place, on the current
+        stream; direction is 0 forward, 1 inverse.  fn=None clears it."""
+        if fn is None:
+            p3_plan_set_z_hook(self.handle, None)
+            self._hook = None
+            return
+        torch = self.torch
+
+        def tramp(data, n, nlines, ls, es, direction, stream, user):
+            try:
+                base = self._bufs[data]
+                flat = base.view(-1).view(self.complex_dtype) if base.dtype != self.complex_dtype else base.view(-1)
+                lines = flat.as_strided((nlines, n), (ls, es))
+                st = (torch.cuda.ExternalStream(stream, device=self.device) if stream
+                      else torch.cuda.default_stream(self.device))
+                with torch.cuda.stream(st):
+                    fn(lines, direction)
+                return 0
+            except BaseException as exc:  # reported after the C call returns
+                self._hook_error = exc
+                return 1
+
+        cb = Z_HOOK(tramp)
+        p3_plan_set_z_hook(self.handle, cb)
+        self._hook = (fn, cb)
+
+    def _call(self, c_fn, inp, out, ws, stream):
+        self._bufs = {t.data_ptr(): t for t in (ws, out) if t is not None}
+        self._hook_error = None
+        try:
+            st = c_fn(self.handle, inp.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
+                      self._stream(stream), check=False)
+        finally:
+            self._bufs = {}
+        if st == P3_ERR_HOOK and self._hook_error is not None:
+            raise P3Error(st, c_fn.__name__) from self._hook_error
+        _check(st, c_fn.__name__)
+
     def launches(self, direction: int) -> int:
         return p3_plan_launches(self.handle, direction)
 
@@ -240,8 +299,7 @@ class Plan:
         out = self.empty_complex() if out is None else out
         self._check_tensor(out, self.complex_shape, self.complex_dtype, "output")
         ws = self.workspace() if ws is None else ws
-        p3_ftran_r2c(self.handle, x.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
-                     self._stream(stream))
+        self._call(p3_ftran_r2c, x, out, ws, stream)
         return out
 
     def complex_view(self, x):
@@ -257,6 +315,5 @@ class Plan:
         out = self.empty_real() if out is None else out
         self._check_tensor(out, self.real_shape, self.real_dtype, "output")
         ws = self.workspace() if ws is None else ws
-        p3_btran_c2r(self.handle, X.data_ptr(), out.data_ptr(), None if ws is None else ws.data_ptr(),
-                     self._stream(stream))
+        self._call(p3_btran_c2r, X, out, ws, stream)
         return out

@@ -106,6 +106,8 @@ def test_null_plan_calls(lib):
     n = ctypes.c_int()
     assert lib.p3_plan_launches(None, 0, ctypes.byref(n)) == P.P3_ERR_INVALID
     assert lib.p3_plan_set_stage_events(None, None, 0) == P.P3_ERR_INVALID
+    assert P.p3_plan_set_z_hook(None, P.Z_HOOK(lambda *a: 0), check=False) == P.P3_ERR_INVALID
+    assert P.p3_status_string(P.P3_ERR_HOOK) == "user Z hook failed"
 
 
 def test_binding_raises_when_library_missing(tmp_path, monkeypatch):
