@@ -81,6 +81,7 @@ typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2, P3_SINE = 3 } p3_ttype;
 /* Plan flags (p3_plan_create). */
 #define P3_FLAG_TC_SPLIT 1u
 #define P3_FLAG_PADDED_REAL 2u
+#define P3_FLAG_NO_FUSE 4u
 
 /* Table 1: storage order of the Z-pencil complex array. */
 typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
@@ -107,6 +108,14 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                place (in == out; Sect. 3.1 in-place transforms).  Neither
  *                direction then needs a workspace; out of place the inverse
  *                works in its output buffer and leaves the input untouched.
+ *              P3_FLAG_NO_FUSE: launch the X and Y stages separately.  By
+ *                default, where a fused kernel exists (FP32, even Nx with
+ *                Nx/2 and Ny in {256, 512, 1024}, FFT in Y, no padded rows,
+ *                no tensor-core split), the X and Y stages of each direction
+ *                run as one persistent launch that works z-plane by z-plane
+ *                so the second stage reads the first one's output from L2.
+ *                Its CTAs wait on one another with bounded waits; see
+ *                p3_plan_wait_status().
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.
@@ -174,6 +183,35 @@ p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len);
 /* Number of kernel launches one ftran (dir = 0) or btran (dir = 1) makes
    (with the Z hook set, if one is). */
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
+
+/*
+ * Plane-fused X + Y launches (no paper counterpart; see P3_FLAG_NO_FUSE):
+ * their CTAs wait, with a bounded number of polls, for the tiles of the same
+ * z-plane that other CTAs compute.  A wait that gives up marks the plan's
+ * device status word, skips its tile (that call's output is then invalid)
+ * and lets the launch finish.  p3_plan_wait_status() synchronises with the
+ * device, returns P3_ERR_TIMEOUT if any wait of this plan gave up since the
+ * last check (and clears the mark), else P3_OK; P3_ERR_INVALID for NULL.
+ */
+p3_status p3_plan_wait_status(p3_plan plan);
+
+/*
+ * Tuning of the plane-fused launches: the consumer tiles of z-plane p are
+ * queued behind the producer tiles of plane p + lag.  A larger lag makes
+ * waits rarer, a smaller one keeps fewer planes in flight in L2.  lag = 0
+ * restores the plan's default; values above Nz act as Nz.  No effect on
+ * plans without fused launches.  P3_ERR_INVALID for NULL or lag < 0.
+ */
+p3_status p3_plan_set_fused_lag(p3_plan plan, int lag);
+
+/*
+ * Test support for the bounded waits: spin_limit polls (>= 1; default
+ * 2^23, over a second) before a wait gives up, and `extra` added to the
+ * count of finished tiles a wait needs (0 by default; any extra > 0 makes
+ * every wait run out, which is how the tests check the error path).
+ * P3_ERR_INVALID for NULL or spin_limit == 0.
+ */
+p3_status p3_plan_set_wait_limits(p3_plan plan, unsigned spin_limit, unsigned extra);
 
 /*
  * p3_z_hook -- a user transform in place of an EMPTY third dimension

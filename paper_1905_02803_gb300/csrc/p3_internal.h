@@ -103,6 +103,42 @@ bool pow2_configure(StageArgs& a, size_t csize);
 cudaError_t pow2_prepare();
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t s);
 
+// Fused X + Y stages over z-planes (p3_fused.cu).  One persistent launch
+// whose CTAs take tasks from a queue in ticket order: the producer tasks of
+// planes 0 .. lag-1, then for p = lag .. Nz-1 the producer tasks of plane p
+// followed by the consumer tasks of plane p - lag, then the consumer tasks
+// of the last lag planes.
+// Forward the producers are X r2c row tiles and the consumers Y column tiles
+// (in place); inverse the producers are Y column tiles and the consumers X
+// c2r row tiles.  A consumer waits (bounded) until every producer of its
+// plane has finished; the plane is then still in L2.
+struct PlaneArgs {
+    StageArgs x;          // the whole X stage (rows map over Ny*Nz rows)
+    StageArgs y;          // the Y stage of one plane (H lines), in place
+    int dir;              // 0 forward, 1 inverse
+    int nplanes;          // Nz
+    int xt, yt;           // X row tiles / Y column tiles per plane
+    int rows;             // Ny: X rows per plane
+    long long yoff;       // Ny * H: complex elements per plane
+    unsigned* ctr;        // [0] ticket, [1 + p] producers done of plane p (zeroed before launch)
+    unsigned* err;        // set non-zero when a wait gives up
+    unsigned spin_limit;  // polls before a wait gives up
+    unsigned extra;       // added to the producer count a consumer waits for (0; > 0 only in tests)
+    int lag;              // consumers of plane p follow the producers of plane p + lag (1 <= lag <= nplanes)
+    int grid;             // persistent CTAs
+    int nt;               // threads per CTA
+    int bx, by;           // rows per X tile, lines per Y tile
+    size_t smem;
+    int kx, ky;           // row / column line lengths (complex points)
+};
+
+// Returns true when a plane-fused kernel exists for these X and Y stages;
+// fills f (except buffers and counters).
+bool fused_configure(PlaneArgs& f, const StageArgs& x, const StageArgs& y, int dir, size_t csize);
+cudaError_t fused_prepare();
+cudaError_t fused_launch(const PlaneArgs& f, cudaStream_t s);
+
+
 // Tensor-core split-precision kernels (p3_tc.cu): FP32 1024-point columns.
 bool tc_configure(StageArgs& a, size_t csize);
 cudaError_t tc_prepare();

@@ -43,6 +43,8 @@ struct Stage {
     int src, dst;       // Buf roles
     const char* name;
     double bytes;       // algorithmic HBM bytes of one launch
+    bool fused;         // plane-fused X + Y launch (f); a is its X stage
+    p3::PlaneArgs f;
 };
 
 struct TableKey {
@@ -71,6 +73,10 @@ struct p3_plan_s {
     std::vector<Stage> st[3];
     p3_z_hook hook;
     void* hook_user;
+    size_t ctr_off;     // byte offset of the fused kernels' counters in the workspace
+    unsigned* derr;     // device word: a bounded wait of a fused kernel gave up
+    unsigned spin_limit, wait_extra;
+    int fused_lag_default[3];
     size_t ws_bytes;
     double scale;
     bool padded;  // real rows of 2H values (in-place capable, XYZ layout)
@@ -361,7 +367,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
 {
     if (!out) return P3_ERR_INVALID;
     *out = NULL;
-    if (!ttype || nx < 1 || ny < 1 || nz < 1 || (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL)))
+    if (!ttype || nx < 1 || ny < 1 || nz < 1 ||
+        (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL | P3_FLAG_NO_FUSE)))
         return P3_ERR_INVALID;
     if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
     if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
@@ -391,6 +398,10 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     P->dtab = NULL;
     P->hook = NULL;
     P->hook_user = NULL;
+    P->ctr_off = 0;
+    P->derr = NULL;
+    P->spin_limit = 1u << 23;
+    P->wait_extra = 0;
     P->timing = false;
     memset(P->events, 0, sizeof(P->events));
     const long long H = P->H, NY = ny, NZ = nz, NX = nx;
@@ -451,6 +462,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         }
         Stage s;
         s.a = a; s.src = src; s.dst = dst; s.name = name; s.bytes = bytes;
+        s.fused = false;
         P->st[dir].push_back(s);
         pend[dir].push_back(pd);
     };
@@ -541,11 +553,32 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         delete P;
         return rc;
     }
+    // ---- plane-fused X + Y launches ----------------------------------------
+    // fwd: stages 0 (X, src -> work) and 1 (Y in place on work); inverse and
+    // hook-mode inverse: stages 1 (Y in place on work) and 2 (X, work -> out)
+    int fuse_at[3] = {-1, -1, -1};
+    p3::PlaneArgs fcfg[3];
+    const bool may_fuse = !(flags & (P3_FLAG_NO_FUSE | P3_FLAG_PADDED_REAL)) && ttype[1] == P3_FFT && ny > 1;
+    for (int d = 0; may_fuse && d < 3; ++d) {
+        const int i = d == 0 ? 0 : 1;
+        auto& v = P->st[d];
+        if ((int)v.size() < i + 2) continue;
+        const Stage& s0 = v[i];
+        const Stage& s1 = v[i + 1];
+        const Stage& sx = d == 0 ? s0 : s1;
+        const Stage& sy = d == 0 ? s1 : s0;
+        if (sy.src != sy.dst || (d == 0 ? sx.dst != sy.src : sx.src != sy.dst)) continue;
+        if (p3::fused_configure(fcfg[d], sx.a, sy.a, d == 0 ? 0 : 1, P->csize)) fuse_at[d] = i;
+    }
+    const bool any_fused = fuse_at[0] >= 0 || fuse_at[1] >= 0 || fuse_at[2] >= 0;
     bool need_ws = false;
     for (int d = 0; d < 3; ++d)
         for (auto& s : P->st[d])
             if (s.src == BUF_WS || s.dst == BUF_WS) need_ws = true;
-    P->ws_bytes = need_ws ? (size_t)P->csize * (size_t)H * (size_t)NY * (size_t)NZ : 0;
+    const size_t cbytes = (size_t)P->csize * (size_t)H * (size_t)NY * (size_t)NZ;
+    P->ctr_off = need_ws ? (cbytes + 255) / 256 * 256 : 0;
+    P->ws_bytes = (need_ws ? cbytes : 0);
+    if (any_fused) P->ws_bytes = P->ctr_off + (sizeof(unsigned) * (size_t)(NZ + 1) + 255) / 256 * 256;
 
     // ---- device tables ------------------------------------------------------
     if (cudaGetDevice(&P->device) != cudaSuccess) {
@@ -598,6 +631,58 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.twm = resolve(pd.twm);
         }
     }
+    for (int d = 0; d < 3; ++d) {
+        const int i = fuse_at[d];
+        if (i < 0) continue;
+        auto& v = P->st[d];
+        Stage& sx = d == 0 ? v[i] : v[i + 1];
+        Stage& sy = d == 0 ? v[i + 1] : v[i];
+        p3::PlaneArgs f = fcfg[d];
+        f.x = sx.a;
+        f.y = sy.a;
+        f.y.nlines = H;  // one plane's Y lines: L = x, in place
+        f.y.in = LineMap{H, 0, 1, H};
+        f.y.out = f.y.in;
+        f.nplanes = nz;
+        f.rows = ny;
+        f.yoff = NY * H;
+        f.xt = (int)((NY + f.bx - 1) / f.bx);
+        f.yt = (int)((H + f.by - 1) / f.by);
+        // lag: about three grid-fulls of tickets between a plane's last
+        // producer and its first consumer, with the planes in flight
+        // (lag + 1 of them) within 48 MB of the 129 MB L2
+        {
+            const long long per = f.xt + f.yt;
+            long long lag = (3LL * f.grid + per - 1) / per + 1;
+            const long long plane_bytes = (long long)P->csize * NY * H;
+            const long long cap = (48LL << 20) / (plane_bytes > 0 ? plane_bytes : 1) - 1;
+            if (lag > cap) lag = cap;
+            if (lag > nz) lag = nz;
+            if (lag < 1) lag = 1;
+            f.lag = (int)lag;
+        }
+        P->fused_lag_default[d] = f.lag;
+        Stage m = sx;
+        m.src = d == 0 ? sx.src : sy.src;
+        m.dst = sx.dst;
+        m.name = d == 0 ? "xy_fused" : "yx_fused_inv";
+        m.bytes = creal + ccplx;
+        m.fused = true;
+        m.f = f;
+        v.erase(v.begin() + i, v.begin() + i + 2);
+        v.insert(v.begin() + i, m);
+    }
+    if (any_fused) {
+        cudaError_t ce = cudaMalloc(&P->derr, 256);
+        if (ce == cudaSuccess) ce = cudaMemset(P->derr, 0, 256);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            if (P->dtab) cudaFree(P->dtab);
+            if (P->derr) cudaFree(P->derr);
+            delete P;
+            return P3_ERR_NOMEM;
+        }
+    }
     // ---- description ----------------------------------------------------------
     char line[512];
     for (int d = 0; d < 2; ++d) {
@@ -607,6 +692,16 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         P->desc += line;
         for (auto& s : P->st[d]) {
             const StageArgs& a = s.a;
+            if (s.fused) {
+                const p3::PlaneArgs& f = s.f;
+                snprintf(line, sizeof(line),
+                         "%s %s kernel=plane_fused x_nfft=%d y_nfft=%d planes=%d x_tiles=%d y_tiles=%d lag=%d "
+                         "persistent_ctas=%d threads=%d smem=%zu bytes=%.0f\n",
+                         d == 0 ? "fwd" : "bwd", s.name, f.kx, f.ky, f.nplanes, f.xt, f.yt, f.lag, f.grid, f.nt, f.smem,
+                         s.bytes);
+                P->desc += line;
+                continue;
+            }
             std::string rs;
             if (a.kern != p3::KIND_GENERIC) {
                 // power-of-two kernels: radix E = nfft / tpl while it divides, then the rest
@@ -658,6 +753,14 @@ p3_status p3_plan_destroy(p3_plan plan)
         if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
         cudaGetLastError();
     }
+    if (plan->derr) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != plan->device) cudaSetDevice(plan->device);
+        cudaFree(plan->derr);
+        if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+        cudaGetLastError();
+    }
     delete plan;
     return P3_OK;
 }
@@ -689,7 +792,7 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
     const size_t hook_after = hook ? (dir == 0 ? stages.size() : 1) : 0;
     bool uses_ws = false;
     for (auto& s : stages)
-        if (s.src == BUF_WS || s.dst == BUF_WS) uses_ws = true;
+        if (s.src == BUF_WS || s.dst == BUF_WS || s.fused) uses_ws = true;
     if (uses_ws) {
         if (!ws) return P3_ERR_WORKSPACE;
         if (overlap(ws, P->ws_bytes, in, nin) || overlap(ws, P->ws_bytes, out, nout)) return P3_ERR_INVALID;
@@ -709,7 +812,22 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
         StageArgs a = st.a;
         a.src = bufs[st.src];
         a.dst = bufs[st.dst];
-        const cudaError_t e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
+        cudaError_t e;
+        if (st.fused) {
+            p3::PlaneArgs f = st.f;
+            f.x.src = bufs[st.src];
+            f.x.dst = bufs[st.dst];
+            void* yb = bufs[dir == 0 ? st.dst : st.src];
+            f.y.src = yb;
+            f.y.dst = yb;
+            f.ctr = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ws) + P->ctr_off);
+            f.err = P->derr;
+            f.spin_limit = P->spin_limit;
+            f.extra = P->wait_extra;
+            e = p3::fused_launch(f, s);
+        } else {
+            e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
+        }
         if (e != cudaSuccess) return P3_ERR_CUDA;
         ++i;
         if (hook && (size_t)i == hook_after && call_hook(P, dir, a.dst, stream) != 0) return P3_ERR_HOOK;
@@ -788,6 +906,40 @@ p3_status p3_plan_launches(p3_plan plan, int dir, int* launches)
 {
     if (!plan || !launches || (dir != 0 && dir != 1)) return P3_ERR_INVALID;
     *launches = (int)plan->st[dir == 1 && plan->hook ? 2 : dir].size();
+    return P3_OK;
+}
+
+p3_status p3_plan_wait_status(p3_plan plan)
+{
+    if (!plan) return P3_ERR_INVALID;
+    if (!plan->derr) return P3_OK;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, plan->derr, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return P3_ERR_CUDA;
+    }
+    if (!v) return P3_OK;
+    if (cudaMemset(plan->derr, 0, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return P3_ERR_CUDA;
+    }
+    return P3_ERR_TIMEOUT;
+}
+
+p3_status p3_plan_set_fused_lag(p3_plan plan, int lag)
+{
+    if (!plan || lag < 0) return P3_ERR_INVALID;
+    for (int d = 0; d < 3; ++d)
+        for (auto& s : plan->st[d])
+            if (s.fused) s.f.lag = lag == 0 ? plan->fused_lag_default[d] : (lag < s.f.nplanes ? lag : s.f.nplanes);
+    return P3_OK;
+}
+
+p3_status p3_plan_set_wait_limits(p3_plan plan, unsigned spin_limit, unsigned extra)
+{
+    if (!plan || spin_limit == 0) return P3_ERR_INVALID;
+    plan->spin_limit = spin_limit;
+    plan->wait_extra = extra;
     return P3_OK;
 }
 

@@ -104,17 +104,35 @@ __device__ __forceinline__ long long lbase(const LineMap& m, long long L)
     return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
 }
 
-// Line of tile lane l (see StageArgs::gcount); returns false past the end.
-__device__ __forceinline__ bool tile_line(const StageArgs& a, int B, int l, long long* L)
+// Line of lane l of tile `tile` (see StageArgs::gcount); false past the end.
+__device__ __forceinline__ bool tile_line(const StageArgs& a, int B, long long tile, int l, long long* L)
 {
     if (a.gcount > 0) {
-        const long long g = blockIdx.x % a.gcount;
-        const int x = (int)(blockIdx.x / a.gcount) * B + l;
+        const long long g = tile % a.gcount;
+        const int x = (int)(tile / a.gcount) * B + l;
         *L = g * a.glen + x;
         return x < a.glen;
     }
-    *L = (long long)blockIdx.x * B + l;
+    *L = tile * B + l;
     return *L < a.nlines;
+}
+
+// Cache policy of a tile's global loads / stores.  Loads: LD_CG through L2
+// only (data another CTA of the same launch wrote: the SM's L1 may hold
+// stale sectors of it); LD_CS streaming (read once, evict first).  Stores:
+// ST_CS streaming (not read again soon).
+enum { LD_DEF = 0, LD_CG = 1, LD_CS = 2 };
+enum { ST_DEF = 0, ST_CS = 1 };
+template <int LP, class C> __device__ __forceinline__ C ldx(const C* p)
+{
+    if constexpr (LP == LD_CG) return __ldcg(p);
+    else if constexpr (LP == LD_CS) return __ldcs(p);
+    else return *p;
+}
+template <int SP, class C> __device__ __forceinline__ void stx(C* p, const C& v)
+{
+    if constexpr (SP == ST_CS) __stcs(p, v);
+    else *p = v;
 }
 
 // twiddle multiply of pass P for butterfly b (tw[k] = exp(-2 pi i k / twn),
@@ -193,9 +211,11 @@ template <> struct Vec4<float> { typedef float4 t; };
 // SYM 0: plain line; 1: Chebyshev even extension (DCT-I of M + 1 points);
 // 2: odd extension (DST-I of M - 1 points: element e reads 0 at e = 0, M,
 // x[e - 1] below M and -x[N - 1 - e] above; output k is i times bin k + 1).
-template <typename T, int N, int E, int B, int MODE, bool INV, int SYM>
-__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
-    col_kernel(const __grid_constant__ StageArgs a)
+// One tile of B lines (tile index `tile`, lines offset by `off` elements in
+// both arrays); s: the tile's shared memory.
+template <typename T, int N, int E, int B, int MODE, bool INV, int SYM, int LP = LD_DEF, int SP = ST_DEF>
+__device__ __forceinline__ void col_tile(const StageArgs& a, long long tile, long long off,
+                                         typename CxT<T>::t* s)
 {
     static_assert(SYM != 2 || !INV, "the sine transform always runs with the forward sign");
     constexpr bool DCT = SYM == 1, DST = SYM == 2;
@@ -206,18 +226,16 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     typedef ColSlot<T, B, SWZ> S;
     typedef EF<T, N, E, B> Ef;
     constexpr int M = N / 2;  // Chebyshev lines hold M + 1 points
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x, l = tid % B, t = tid / B;
     long long L;
-    const bool valid = tile_line(a, B, l, &L);
+    const bool valid = tile_line(a, B, tile, l, &L);
     const C zero = mk<C>((T)0, (T)0);
     const C* tw = static_cast<const C*>(a.tw);
     C v[E];
     typedef PassIdx<N, E, 0> P0;
 
     if constexpr (MODE != 2) {
-        const C* src = static_cast<const C*>(a.src) + (valid ? lbase(a.in, L) : 0);
+        const C* src = static_cast<const C*>(a.src) + off + (valid ? lbase(a.in, L) : 0);
         const long long es = a.in.es;
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
@@ -227,37 +245,37 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                 const int e = t + K;
                 C x;
                 if constexpr (DST) {
-                    const long long off = (long long)(e < M ? e - 1 : N - 1 - e) * es;
-                    x = (valid && e != 0 && e != M) ? src[off] : zero;
+                    const long long o = (long long)(e < M ? e - 1 : N - 1 - e) * es;
+                    x = (valid && e != 0 && e != M) ? ldx<LP>(src + o) : zero;
                     if (e > M) x = mk<C>(-x.x, -x.y);
                 } else {
                     // even extension of a Chebyshev line: element e > M reads N - e
-                    const long long off = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
-                    x = valid ? src[off] : zero;
+                    const long long o = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
+                    x = valid ? ldx<LP>(src + o) : zero;
                 }
                 v[b * P0::R + r] = INV ? swp(x) : x;
             }
     } else {
         const int le = Ef::line(tid);
         long long Le;
-        const bool ve = tile_line(a, B, le, &Le);
-        const C* src = static_cast<const C*>(a.src) + (ve ? lbase(a.in, Le) : 0);
+        const bool ve = tile_line(a, B, tile, le, &Le);
+        const C* src = static_cast<const C*>(a.src) + off + (ve ? lbase(a.in, Le) : 0);
         if constexpr (DST) {
             for (int c = Ef::chunk0(tid); c < N; c += Ef::STEP) {
-                C x = (ve && c != 0 && c != M) ? src[c < M ? c - 1 : N - 1 - c] : zero;
+                C x = (ve && c != 0 && c != M) ? ldx<LP>(src + (c < M ? c - 1 : N - 1 - c)) : zero;
                 s[S::at(c, le)] = c > M ? mk<C>(-x.x, -x.y) : x;
             }
         } else if constexpr (DCT || Ef::VEC == 1) {
             for (int c = Ef::chunk0(tid); c < N; c += Ef::STEP) {
                 const int ee = DCT ? (c <= M ? c : N - c) : c;
-                C x = ve ? src[ee] : zero;
+                C x = ve ? ldx<LP>(src + ee) : zero;
                 s[S::at(c, le)] = INV ? swp(x) : x;
             }
         } else {
             typedef typename Vec4<T>::t V;
             const V* src4 = reinterpret_cast<const V*>(src);
             for (int c = Ef::chunk0(tid); c < N / 2; c += Ef::STEP) {
-                V q = ve ? src4[c] : V{(T)0, (T)0, (T)0, (T)0};
+                V q = ve ? ldx<LP>(src4 + c) : V{(T)0, (T)0, (T)0, (T)0};
                 C x0 = mk<C>(q.x, q.y), x1 = mk<C>(q.z, q.w);
                 s[S::at(2 * c, le)] = INV ? swp(x0) : x0;
                 s[S::at(2 * c + 1, le)] = INV ? swp(x1) : x1;
@@ -275,7 +293,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     typedef PassIdx<N, E, NP - 1> PLast;
     if constexpr (MODE != 1) {
         if (valid) {
-            C* dst = static_cast<C*>(a.dst) + lbase(a.out, L);
+            C* dst = static_cast<C*>(a.dst) + off + lbase(a.out, L);
             const long long es = a.out.es;
             const int u = PLast::out_u(t);
 #pragma unroll
@@ -285,9 +303,9 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                     const int e = u + PLast::out_K(b, r);
                     const C x = v[b * PLast::R + r];
                     if constexpr (DST) {
-                        if (e >= 1 && e < M) dst[(long long)(e - 1) * es] = mk<C>(-x.y, x.x);
+                        if (e >= 1 && e < M) stx<SP>(dst + (long long)(e - 1) * es, mk<C>(-x.y, x.x));
                     } else {
-                        if (!DCT || e <= M) dst[(long long)e * es] = INV ? swp(x) : x;
+                        if (!DCT || e <= M) stx<SP>(dst + (long long)e * es, INV ? swp(x) : x);
                     }
                 }
         }
@@ -304,8 +322,8 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         __syncthreads();
         const int le = Ef::line(tid);
         long long Le;
-        if (tile_line(a, B, le, &Le)) {
-            C* dst = static_cast<C*>(a.dst) + lbase(a.out, Le);
+        if (tile_line(a, B, tile, le, &Le)) {
+            C* dst = static_cast<C*>(a.dst) + off + lbase(a.out, Le);
             if constexpr (DST) {
                 for (int c = Ef::chunk0(tid); c < M - 1; c += Ef::STEP) {
                     const C x = s[S::at(c + 1, le)];
@@ -330,6 +348,14 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
             }
         }
     }
+}
+
+template <typename T, int N, int E, int B, int MODE, bool INV, int SYM>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    col_kernel(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col_tile<T, N, E, B, MODE, INV, SYM>(a, blockIdx.x, 0, reinterpret_cast<typename CxT<T>::t*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -535,20 +561,18 @@ template <class C, class T, int N, int E, int NP> struct RowRest<C, T, N, E, NP,
     static __device__ __forceinline__ void run(C (&)[E], C*, int, const C*) {}
 };
 
-template <typename T, int N, int E, int B, int OPR>
-__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
-    row_kernel(const __grid_constant__ StageArgs a)
+// Rows L0 .. L0 + B - 1 (those below Lend) of a row stage; s: the tile's
+// shared memory.
+template <typename T, int N, int E, int B, int OPR, int LP = LD_DEF, int SP = ST_DEF>
+__device__ __forceinline__ void row_tile(const StageArgs& a, long long L0, long long Lend, typename CxT<T>::t* s)
 {
     typedef typename CxT<T>::t C;
     typedef P2<N, E> PL;
     constexpr int TPL = PL::TPL, NP = PL::NPASS;
     typedef RowSlot<N, E> S;
-    constexpr int H = N + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
-    const long long L = (long long)blockIdx.x * B + l;
-    const bool valid = L < a.nlines;
+    const long long L = L0 + l;
+    const bool valid = L < Lend;
     const C zero = mk<C>((T)0, (T)0);
     const C* tw2 = static_cast<const C*>(a.tw2);  // exp(-2 pi i k / 2N), k < 2N
     C* srow = s + l * S::RP;
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
 #pragma unroll
-            for (int r = 0; r < P0::R; ++r) v[b * P0::R + r] = valid ? src[t + P0::in_K(b, r)] : zero;
+            for (int r = 0; r < P0::R; ++r) v[b * P0::R + r] = valid ? ldx<LP>(src + t + P0::in_K(b, r)) : zero;
     } else {
         // Z[k] = (F[k] + conj F[N-k]) + i (F[k] - conj F[N-k]) exp(+2 pi i k / 2N),
         // imaginary parts of F[0] and F[N] dropped; inverse via swp
@@ -572,8 +596,8 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 #pragma unroll
             for (int r = 0; r < P0::R; ++r) {
                 const int k = t + P0::in_K(b, r);
-                C A = valid ? src[k] : zero;
-                C Bc = valid ? cnj(src[N - k]) : zero;
+                C A = valid ? ldx<LP>(src + k) : zero;
+                C Bc = valid ? cnj(ldx<LP>(src + (N - k))) : zero;
                 if (k == 0) {
                     A.y = (T)0;
                     Bc.y = (T)0;
@@ -603,7 +627,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                 const C zk = srow[S::at(k == N ? 0 : k)];
                 const C zm = cnj(srow[S::at(k == 0 ? 0 : N - k)]);
                 const C p = mul(ldg(tw2 + k), sub(zk, zm));
-                dst[k] = mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x));
+                stx<SP>(dst + k, mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x)));
             }
         }
     } else {
@@ -613,9 +637,18 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 #pragma unroll
             for (int b = 0; b < PLast::BM; ++b)
 #pragma unroll
-                for (int r = 0; r < PLast::R; ++r) dst[u + PLast::out_K(b, r)] = swp(v[b * PLast::R + r]);
+                for (int r = 0; r < PLast::R; ++r) stx<SP>(dst + u + PLast::out_K(b, r), swp(v[b * PLast::R + r]));
         }
     }
+}
+
+template <typename T, int N, int E, int B, int OPR>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    row_kernel(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    row_tile<T, N, E, B, OPR>(a, (long long)blockIdx.x * B, a.nlines,
+                              reinterpret_cast<typename CxT<T>::t*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------

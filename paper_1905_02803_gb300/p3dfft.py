@@ -21,11 +21,14 @@ P3_FFT, P3_CHEB, P3_EMPTY, P3_SINE = 0, 1, 2, 3
 P3_LAYOUT_ZYX, P3_LAYOUT_XYZ = 0, 1
 P3_FLAG_TC_SPLIT = 1
 P3_FLAG_PADDED_REAL = 2
+P3_FLAG_NO_FUSE = 4
 
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
-           "p3_plan_launches", "p3_plan_set_z_hook", "p3_status_string", "p3_version")
+           "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_set_wait_limits",
+           "p3_plan_set_fused_lag",
+           "p3_status_string", "p3_version")
 
 # int hook(void* data, int n, long long nlines, long long line_stride, long long elem_stride,
 #          int dir, void* stream, void* user)
@@ -63,6 +66,9 @@ def load():
     lib.p3_plan_describe.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     lib.p3_plan_launches.argtypes = [P, I, ctypes.POINTER(I)]
     lib.p3_plan_set_z_hook.argtypes = [P, Z_HOOK, P]
+    lib.p3_plan_wait_status.argtypes = [P]
+    lib.p3_plan_set_wait_limits.argtypes = [P, U, U]
+    lib.p3_plan_set_fused_lag.argtypes = [P, I]
     lib.p3_status_string.argtypes = [I]
     lib.p3_status_string.restype = ctypes.c_char_p
     lib.p3_version.argtypes = []
@@ -124,6 +130,26 @@ def p3_plan_set_z_hook(plan, hook, user=None, check=True):
     st = load().p3_plan_set_z_hook(plan, hook if hook is not None else Z_HOOK(), user)
     if check:
         _check(st, "p3_plan_set_z_hook")
+    return st
+
+
+def p3_plan_wait_status(plan) -> int:
+    """P3_OK, or P3_ERR_TIMEOUT when a bounded wait of a fused launch gave up
+    since the last check (synchronises with the device)."""
+    return load().p3_plan_wait_status(plan)
+
+
+def p3_plan_set_wait_limits(plan, spin_limit, extra=0, check=True):
+    st = load().p3_plan_set_wait_limits(plan, int(spin_limit), int(extra))
+    if check:
+        _check(st, "p3_plan_set_wait_limits")
+    return st
+
+
+def p3_plan_set_fused_lag(plan, lag, check=True):
+    st = load().p3_plan_set_fused_lag(plan, int(lag))
+    if check:
+        _check(st, "p3_plan_set_fused_lag")
     return st
 
 

@@ -61,7 +61,7 @@ FFT3 = (P.P3_FFT, P.P3_FFT, P.P3_FFT)
     ((8, -1, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, 7, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, FFT3, 5, 0), P.P3_ERR_INVALID),
-    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 4), P.P3_ERR_INVALID),
+    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 8), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, P.P3_FLAG_PADDED_REAL), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_FFT, 9), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 1, P.P3_F64, (P.P3_FFT, P.P3_FFT, P.P3_CHEB), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
@@ -108,6 +108,9 @@ def test_null_plan_calls(lib):
     assert lib.p3_plan_set_stage_events(None, None, 0) == P.P3_ERR_INVALID
     assert P.p3_plan_set_z_hook(None, P.Z_HOOK(lambda *a: 0), check=False) == P.P3_ERR_INVALID
     assert P.p3_status_string(P.P3_ERR_HOOK) == "user Z hook failed"
+    assert P.p3_plan_wait_status(None) == P.P3_ERR_INVALID
+    assert P.p3_plan_set_wait_limits(None, 10, 0, check=False) == P.P3_ERR_INVALID
+    assert P.p3_plan_set_fused_lag(None, 1, check=False) == P.P3_ERR_INVALID
 
 
 def test_binding_raises_when_library_missing(tmp_path, monkeypatch):
