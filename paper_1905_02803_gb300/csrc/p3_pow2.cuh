@@ -533,13 +533,22 @@ template <int N, int E> struct RowSlot {
     }
 };
 
+// A row's TPL threads lie in one warp when TPL <= 32 (the B rows of a tile
+// never share shared memory), so the row exchanges need only a warp
+// barrier; longer rows span warps and use the block barrier.
+template <int TPL> __device__ __forceinline__ void row_sync()
+{
+    if constexpr (TPL <= 32 && 32 % TPL == 0) __syncwarp();
+    else __syncthreads();
+}
+
 template <class C, class T, int N, int E, int P, int NP> struct RowRest {
     static __device__ __forceinline__ void run(C (&v)[E], C* s, int t, const C* tw)
     {
         typedef PassIdx<N, E, P - 1> Pr;
         typedef PassIdx<N, E, P> Cu;
         typedef RowSlot<N, E> S;
-        __syncthreads();
+        row_sync<N / E>();
         {
             const int u = Pr::out_u(t);
 #pragma unroll
@@ -548,7 +557,7 @@ template <class C, class T, int N, int E, int P, int NP> struct RowRest {
                 for (int r = 0; r < Pr::R; ++r)
                     s[S::at_k(u, Pr::out_K(b, r), Pr::OUT_UA)] = v[b * Pr::R + r];
         }
-        __syncthreads();
+        row_sync<N / E>();
 #pragma unroll
         for (int b = 0; b < Cu::BM; ++b)
 #pragma unroll
@@ -611,7 +620,7 @@ __device__ __forceinline__ void row_tile(const StageArgs& a, long long L0, long 
     RowRest<C, T, N, E, 1, NP>::run(v, srow, t, tw2);
 
     if constexpr (OPR == 0) {
-        __syncthreads();
+        row_sync<N / E>();
         {
             const int u = PLast::out_u(t);
 #pragma unroll
@@ -620,7 +629,7 @@ __device__ __forceinline__ void row_tile(const StageArgs& a, long long L0, long 
                 for (int r = 0; r < PLast::R; ++r)
                     srow[S::at_k(u, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
         }
-        __syncthreads();
+        row_sync<N / E>();
         if (valid) {
             C* dst = static_cast<C*>(a.dst) + L * a.out.lstride;
             for (int k = t; k <= N; k += TPL) {
