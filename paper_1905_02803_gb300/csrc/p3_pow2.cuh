@@ -542,7 +542,7 @@ template <int TPL> __device__ __forceinline__ void row_sync()
     else __syncthreads();
 }
 
-template <class C, class T, int N, int E, int P, int NP> struct RowRest {
+template <class C, class T, int N, int E, int P, int NP, int TS = 2> struct RowRest {
     static __device__ __forceinline__ void run(C (&v)[E], C* s, int t, const C* tw)
     {
         typedef PassIdx<N, E, P - 1> Pr;
@@ -562,11 +562,11 @@ template <class C, class T, int N, int E, int P, int NP> struct RowRest {
         for (int b = 0; b < Cu::BM; ++b)
 #pragma unroll
             for (int r = 0; r < Cu::R; ++r) v[b * Cu::R + r] = s[S::at_k(t, Cu::in_K(b, r), 1)];
-        pass_compute<C, T, N, E, P>(v, t, tw, 2);
-        RowRest<C, T, N, E, P + 1, NP>::run(v, s, t, tw);
+        pass_compute<C, T, N, E, P>(v, t, tw, TS);
+        RowRest<C, T, N, E, P + 1, NP, TS>::run(v, s, t, tw);
     }
 };
-template <class C, class T, int N, int E, int NP> struct RowRest<C, T, N, E, NP, NP> {
+template <class C, class T, int N, int E, int NP, int TS> struct RowRest<C, T, N, E, NP, NP, TS> {
     static __device__ __forceinline__ void run(C (&)[E], C*, int, const C*) {}
 };
 
@@ -661,6 +661,89 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 }
 
 // ---------------------------------------------------------------------------
+// ZYX-load kernel with row-style lines (the inverse Z stage reading the
+// STRIDE1 layout of Table 1).  Each input line is contiguous there, so a
+// line's TPL threads load it like an X row (coalesced, straight into
+// registers) and run the passes with exchanges private to the line's warp;
+// the results cross shared memory once, to be stored with lanes across the
+// tile's B adjacent lines (B-wide runs of the XYZ output).  Input lines must
+// have unit element stride.  SYM as in col_tile.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int E, int B, bool INV, int SYM>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    zrow_kernel(const __grid_constant__ StageArgs a)
+{
+    static_assert(SYM != 2 || !INV, "the sine transform always runs with the forward sign");
+    constexpr bool DCT = SYM == 1, DST = SYM == 2;
+    typedef typename CxT<T>::t C;
+    typedef P2<N, E> PL;
+    constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL;
+    constexpr int M = N / 2;
+    constexpr int LD = B + 1;  // result tile: element e of line l at e * LD + l
+    static_assert(NT % B == 0, "store lanes keep their line");
+    typedef RowSlot<N, E> S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
+    const long long L0 = (long long)blockIdx.x * B;
+    const long long L = L0 + l;
+    const bool valid = L < a.nlines;
+    const C zero = mk<C>((T)0, (T)0);
+    const C* tw = static_cast<const C*>(a.tw);
+    C v[E];
+    typedef PassIdx<N, E, 0> P0;
+    typedef PassIdx<N, E, NP - 1> PLast;
+    {
+        const C* src = static_cast<const C*>(a.src) + (valid ? lbase(a.in, L) : 0);
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) {
+                const int e = t + P0::in_K(b, r);
+                C x;
+                if constexpr (DST) {
+                    x = (valid && e != 0 && e != M) ? src[e < M ? e - 1 : N - 1 - e] : zero;
+                    if (e > M) x = mk<C>(-x.x, -x.y);
+                } else {
+                    x = valid ? src[DCT ? (e <= M ? e : N - e) : e] : zero;
+                }
+                v[b * P0::R + r] = INV ? swp(x) : x;
+            }
+    }
+    pass_compute<C, T, N, E, 0>(v, t, tw, 1);
+    RowRest<C, T, N, E, 1, NP, 1>::run(v, s + l * S::RP, t, tw);
+    __syncthreads();  // the result tile overlaps other lines' exchange rows
+    {
+        const int u = PLast::out_u(t);
+#pragma unroll
+        for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < PLast::R; ++r) s[(u + PLast::out_K(b, r)) * LD + l] = v[b * PLast::R + r];
+    }
+    __syncthreads();
+    constexpr int NOUT = DCT ? M + 1 : DST ? M - 1 : N;
+    const int ll = tid % B;
+    const long long LL = L0 + ll;
+    if (LL < a.nlines) {
+        C* dst = static_cast<C*>(a.dst) + lbase(a.out, LL);
+        const long long es = a.out.es;
+        for (int c = tid / B; c < NOUT; c += NT / B) {
+            C x = s[(DST ? c + 1 : c) * LD + ll];
+            if constexpr (DST) x = mk<C>(-x.y, x.x);
+            else if constexpr (INV) x = swp(x);
+            dst[(long long)c * es] = x;
+        }
+    }
+}
+
+template <typename T, int N, int E, int B> __host__ __device__ constexpr size_t zrow_smem()
+{
+    typedef typename CxT<T>::t C;
+    const size_t ex = (size_t)B * (size_t)RowSlot<N, E>::RP, res = (size_t)N * (size_t)(B + 1);
+    return (ex > res ? ex : res) * sizeof(C);
+}
+
+// ---------------------------------------------------------------------------
 // Tile shapes per precision and length
 // ---------------------------------------------------------------------------
 #ifndef P3_COL_E32
@@ -687,11 +770,21 @@ template <typename T> __host__ __device__ constexpr int col_B(int N)
 #ifndef P3_PL_E
 #define P3_PL_E 16
 #endif
+template <typename T> __host__ __device__ constexpr bool col_zrow(int N);
 template <typename T> __host__ __device__ constexpr bool col_pipelined(int N, int mode)
 {
-    return P3_PIPELINE && sizeof(T) == 4 && mode == 2 && N >= 512 && N <= 1024;
+    return P3_PIPELINE && sizeof(T) == 4 && mode == 2 && N >= 512 && N <= 1024 && !col_zrow<T>(N);
 }
 template <typename T> __host__ __device__ constexpr int col_pl_E(int N, int mode) { return mode == 2 ? 16 : P3_PL_E; }
+// Row-style ZYX-load kernel for FP32 lines of 256 .. 1024 points (a line's
+// threads fit in one warp); it takes precedence over the pipelined one.
+#ifndef P3_ZROW
+#define P3_ZROW 1
+#endif
+template <typename T> __host__ __device__ constexpr bool col_zrow(int N)
+{
+    return P3_ZROW && sizeof(T) == 4 && N >= 256 && N <= 1024;
+}
 #ifndef P3_ROW_E32
 #define P3_ROW_E32 1
 #endif

@@ -17,6 +17,13 @@ template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
     else
         return nullptr;
 }
+template <int N, bool INV, int SYM> void* zrow_fn()
+{
+    if constexpr (col_zrow<float>(N))
+        return (void*)zrow_kernel<float, N, row_E<float>(N), row_B<float>(N), INV, SYM>;
+    else
+        return nullptr;
+}
 template <int N, int OPR> void* row_fn() { return (void*)row_kernel<float, N, row_E<float>(N), row_B<float>(N), OPR>; }
 
 // sym: 0 plain, 1 Chebyshev (DCT-I), 2 sine (DST-I, forward sign only)
@@ -29,7 +36,13 @@ template <int N> void* pick_n(int kind, bool inv, int sym, bool pl)
     switch (kind) {
     case KIND_COL_DD: return pl ? P3_COL_PICK(col_pl_fn, 0) : P3_COL_PICK(col_fn, 0);
     case KIND_COL_DS: return pl ? P3_COL_PICK(col_pl_fn, 1) : P3_COL_PICK(col_fn, 1);
-    case KIND_COL_SD: return pl ? P3_COL_PICK(col_pl_fn, 2) : P3_COL_PICK(col_fn, 2);
+    case KIND_COL_SD:
+        if (col_zrow<float>(N))
+            return pl ? nullptr
+                      : (sym == 2 ? (inv ? (void*)nullptr : zrow_fn<N, false, 2>())
+                         : inv ? (sym ? zrow_fn<N, true, 1>() : zrow_fn<N, true, 0>())
+                               : (sym ? zrow_fn<N, false, 1>() : zrow_fn<N, false, 0>()));
+        return pl ? P3_COL_PICK(col_pl_fn, 2) : P3_COL_PICK(col_fn, 2);
     case KIND_ROW_R2C: return pl ? nullptr : row_fn<N, 0>();
     case KIND_ROW_C2R: return pl ? nullptr : row_fn<N, 1>();
     default: return nullptr;
@@ -61,6 +74,15 @@ void pow2_shape_f32(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* sm
         *B = row_B<float>(N);
         *tpl = N / E;
         *smem = (size_t)(*B) * (size_t)(N + N / E + 1) * sizeof(float) * 2;
+    } else if (kind == KIND_COL_SD && col_zrow<float>(N)) {
+        const int E = row_E<float>(N);
+        *B = row_B<float>(N);
+        *tpl = N / E;
+        switch (N) {
+        case 256: *smem = zrow_smem<float, 256, row_E<float>(256), row_B<float>(256)>(); break;
+        case 512: *smem = zrow_smem<float, 512, row_E<float>(512), row_B<float>(512)>(); break;
+        default: *smem = zrow_smem<float, 1024, row_E<float>(1024), row_B<float>(1024)>(); break;
+        }
     } else {
         const int mode = kind == KIND_COL_SD ? 2 : kind == KIND_COL_DS ? 1 : 0;
         *B = col_B<float>(N);

@@ -17,6 +17,13 @@ template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
     else
         return nullptr;
 }
+template <int N, bool INV, int SYM> void* zrow_fn()
+{
+    if constexpr (col_zrow<double>(N))
+        return (void*)zrow_kernel<double, N, row_E<double>(N), row_B<double>(N), INV, SYM>;
+    else
+        return nullptr;
+}
 template <int N, int OPR> void* row_fn() { return (void*)row_kernel<double, N, row_E<double>(N), row_B<double>(N), OPR>; }
 
 // sym: 0 plain, 1 Chebyshev (DCT-I), 2 sine (DST-I, forward sign only)
@@ -29,7 +36,13 @@ template <int N> void* pick_n(int kind, bool inv, int sym, bool pl)
     switch (kind) {
     case KIND_COL_DD: return pl ? P3_COL_PICK(col_pl_fn, 0) : P3_COL_PICK(col_fn, 0);
     case KIND_COL_DS: return pl ? P3_COL_PICK(col_pl_fn, 1) : P3_COL_PICK(col_fn, 1);
-    case KIND_COL_SD: return pl ? P3_COL_PICK(col_pl_fn, 2) : P3_COL_PICK(col_fn, 2);
+    case KIND_COL_SD:
+        if (col_zrow<double>(N))
+            return pl ? nullptr
+                      : (sym == 2 ? (inv ? (void*)nullptr : zrow_fn<N, false, 2>())
+                         : inv ? (sym ? zrow_fn<N, true, 1>() : zrow_fn<N, true, 0>())
+                               : (sym ? zrow_fn<N, false, 1>() : zrow_fn<N, false, 0>()));
+        return pl ? P3_COL_PICK(col_pl_fn, 2) : P3_COL_PICK(col_fn, 2);
     case KIND_ROW_R2C: return pl ? nullptr : row_fn<N, 0>();
     case KIND_ROW_C2R: return pl ? nullptr : row_fn<N, 1>();
     default: return nullptr;
@@ -61,6 +74,15 @@ void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* sm
         *B = row_B<double>(N);
         *tpl = N / E;
         *smem = (size_t)(*B) * (size_t)(N + N / E + 1) * sizeof(double) * 2;
+    } else if (kind == KIND_COL_SD && col_zrow<double>(N)) {
+        const int E = row_E<double>(N);
+        *B = row_B<double>(N);
+        *tpl = N / E;
+        switch (N) {
+        case 256: *smem = zrow_smem<double, 256, row_E<double>(256), row_B<double>(256)>(); break;
+        case 512: *smem = zrow_smem<double, 512, row_E<double>(512), row_B<double>(512)>(); break;
+        default: *smem = zrow_smem<double, 1024, row_E<double>(1024), row_B<double>(1024)>(); break;
+        }
     } else {
         const int mode = kind == KIND_COL_SD ? 2 : kind == KIND_COL_DS ? 1 : 0;
         *B = col_B<double>(N);
