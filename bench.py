@@ -584,8 +584,10 @@ def _report_one(name, dims, prec, ttypes, layout, kind, mode="", *, steps, warmu
             "oracle_ms_full": None if t_or is None else round(t_or, 1)}
 
 
-def _report_batch(steps, warmup):
-    """64 independent FP32 transforms of 7-smooth sizes, 64 plain plan launches."""
+def _report_batch(steps, warmup, nstreams=16):
+    """64 independent FP32 transforms of 7-smooth sizes: 64 plans one after
+    another on one stream, and the same plans as one p3_batch over nstreams
+    internal streams; each plain and replayed from a captured CUDA graph."""
     import numpy as np
     import torch
 
@@ -600,50 +602,59 @@ def _report_batch(steps, warmup):
         xs.append(torch.from_numpy(inputs.gaussian_field((nz, ny, nx), seed=k).astype(np.float32)).cuda())
         Xs.append(p.empty_complex())
         ys.append(p.empty_real())
-    def step():
+        p.workspace()
+    batch = P.Batch(plans, nstreams=nstreams)
+
+    def serial():
         for p, x, X, y in zip(plans, xs, Xs, ys):
             p.forward(x, X)
             p.backward(X, y)
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
+
+    def batched():
+        batch.forward(xs, Xs)
+        batch.backward(Xs, ys)
+
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(steps):
-        step()
-    t1.record()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    # the same 384 launches captured once into a CUDA graph and replayed
-    for p in plans:
-        p.workspace()
-    g = torch.cuda.CUDAGraph()
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        step()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
         torch.cuda.synchronize()
-        with torch.cuda.graph(g, stream=s):
-            step()
-    torch.cuda.synchronize()
-    g.replay()
-    torch.cuda.synchronize()
-    t0.record()
-    for _ in range(steps):
-        g.replay()
-    t1.record()
-    torch.cuda.synchronize()
-    ms_graph = t0.elapsed_time(t1) / steps
+        t0.record()
+        for _ in range(steps):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    def graphed(fn):
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                fn()
+        torch.cuda.synchronize()
+        return timed(g.replay)
+
+    ms = timed(serial)
+    ms_graph = graphed(serial)
+    ms_batch = timed(batched)
+    ms_batch_graph = graphed(batched)
     pair_bytes = sum(sum(stage_model_bytes(nx, ny, nz, 4)) for nx, ny, nz in dims)
     peak, _ = peaks()
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
+    best = min(ms, ms_graph, ms_batch, ms_batch_graph)
     launches = sum(p.launches(0) + p.launches(1) for p in plans)
     kinds = sorted({l.split()[2] for p in plans for l in p.describe().splitlines() if "kernel=" in l})
-    return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(ms, 4), "ms_cuda_graph": round(ms_graph, 4),
-            "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
-            "hbm_roofline_frac": round(roof_ms / ms, 4), "launches_per_step": launches, "kernels": kinds,
-            "mode": "64 separate plans, plain launches on one stream"}
+    return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(best, 4),
+            "ms_serial": round(ms, 4), "ms_serial_cuda_graph": round(ms_graph, 4),
+            "ms_batch_streams": round(ms_batch, 4), "ms_batch_streams_cuda_graph": round(ms_batch_graph, 4),
+            "batch_streams": nstreams, "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
+            "hbm_roofline_frac": round(roof_ms / best, 4), "launches_per_step": launches, "kernels": kinds}
 
 
 def run_report(args):

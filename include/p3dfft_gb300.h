@@ -248,6 +248,35 @@ typedef int (*p3_z_hook)(void* data, int n, long long nlines, long long line_str
 p3_status p3_plan_set_z_hook(p3_plan plan, p3_z_hook fn, void* user);
 
 /*
+ * Batched execution of independent plans (no paper counterpart: many 3D
+ * transforms per call).  A batch spreads its plans over `nstreams` internal
+ * streams (largest plans first, each to the least loaded stream), so the
+ * launches of different plans overlap on the GPU.
+ *
+ * p3_batch_create: plans (nplans >= 1, all created on the current device;
+ *   the batch keeps the handles, not copies: destroy the batch first),
+ *   nstreams >= 1 (capped at nplans).  Creates the streams and events.
+ *   P3_ERR_INVALID on bad arguments, P3_ERR_CUDA if a stream or event
+ *   cannot be created.
+ * p3_batch_ftran_r2c / p3_batch_btran_c2r: arrays of nplans pointers in
+ *   plan order: in[i], out[i], ws[i] as p3_ftran_r2c / p3_btran_c2r take
+ *   them for plan i (ws may be NULL when no plan needs a workspace, and
+ *   ws[i] NULL for plans that need none).  Every buffer must be distinct
+ *   from every other plan's (the plans run concurrently).  Stream-ordered on
+ *   `stream`: the batch starts after the work already on `stream` and
+ *   `stream` continues only after every plan finished; capturable into a
+ *   CUDA graph.  Returns the first error of a plan; plans before it were
+ *   enqueued and are still joined back into `stream`.
+ */
+typedef struct p3_batch_s* p3_batch;
+p3_status p3_batch_create(p3_batch* out, int nplans, const p3_plan* plans, int nstreams);
+p3_status p3_batch_destroy(p3_batch batch);
+p3_status p3_batch_ftran_r2c(p3_batch batch, const void* const* in, void* const* out, void* const* ws,
+                             void* stream);
+p3_status p3_batch_btran_c2r(p3_batch batch, const void* const* in, void* const* out, void* const* ws,
+                             void* stream);
+
+/*
  * p3_ftran_r2c_noalloc -- the forward transform of p3_ftran_r2c, but with the
  * workspace taken from a fixed device array built into the library instead
  * of from the caller.  The paper has no counterpart: this exists for callers

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libp3dfft_gb300.so")
 SOURCES = ["p3_plan.cu", "p3_kernels.cu", "p3_pow2.cu", "p3_pow2_f32.cu", "p3_pow2_f64.cu", "p3_noalloc.cu", "p3_tc.cu",
-           "p3_fused.cu"]
+           "p3_fused.cu", "p3_batch.cu"]
 HEADERS = [os.path.join(CSRC, "p3_internal.h"), os.path.join(CSRC, "p3_dft.cuh"), os.path.join(CSRC, "p3_pow2.cuh"), os.path.join(ROOT, "include", "p3dfft_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

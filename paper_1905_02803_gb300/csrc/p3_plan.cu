@@ -960,4 +960,6 @@ p3_status run_direction(p3_plan plan, int dir, const void* in, void* out, void* 
     return run(plan, dir, in, out, ws, stream);
 }
 size_t plan_workspace(p3_plan plan) { return plan ? plan->ws_bytes : 0; }
+double plan_work(p3_plan plan) { return plan ? (double)plan->nx * plan->ny * plan->nz : 0.0; }
+int plan_device(p3_plan plan) { return plan ? plan->device : -1; }
 }  // namespace p3

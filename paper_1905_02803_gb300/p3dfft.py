@@ -27,7 +27,8 @@ EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", 
            "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
            "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_set_wait_limits",
-           "p3_plan_set_fused_lag",
+           "p3_plan_set_fused_lag", "p3_batch_create", "p3_batch_destroy", "p3_batch_ftran_r2c",
+           "p3_batch_btran_c2r",
            "p3_status_string", "p3_version")
 
 # int hook(void* data, int n, long long nlines, long long line_stride, long long elem_stride,
@@ -69,6 +70,10 @@ def load():
     lib.p3_plan_wait_status.argtypes = [P]
     lib.p3_plan_set_wait_limits.argtypes = [P, U, U]
     lib.p3_plan_set_fused_lag.argtypes = [P, I]
+    lib.p3_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P), I]
+    lib.p3_batch_destroy.argtypes = [P]
+    lib.p3_batch_ftran_r2c.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
+    lib.p3_batch_btran_c2r.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.p3_status_string.argtypes = [I]
     lib.p3_status_string.restype = ctypes.c_char_p
     lib.p3_version.argtypes = []
@@ -150,6 +155,40 @@ def p3_plan_set_fused_lag(plan, lag, check=True):
     st = load().p3_plan_set_fused_lag(plan, int(lag))
     if check:
         _check(st, "p3_plan_set_fused_lag")
+    return st
+
+
+def _ptrs(vals):
+    return (ctypes.c_void_p * len(vals))(*[ctypes.c_void_p(v) if v else None for v in vals])
+
+
+def p3_batch_create(plans, nstreams, check=True):
+    """plans: list of plan handles.  Returns (status, batch handle or None)."""
+    h = ctypes.c_void_p()
+    arr = None if plans is None else _ptrs(plans)
+    st = load().p3_batch_create(ctypes.byref(h), 0 if plans is None else len(plans), arr, int(nstreams))
+    if check:
+        _check(st, "p3_batch_create")
+    return st, (h.value if st == P3_OK else None)
+
+
+def p3_batch_destroy(batch):
+    return load().p3_batch_destroy(batch)
+
+
+def p3_batch_ftran_r2c(batch, ins, outs, wss, stream, check=True):
+    st = load().p3_batch_ftran_r2c(batch, None if ins is None else _ptrs(ins), None if outs is None else _ptrs(outs),
+                                   None if wss is None else _ptrs(wss), stream)
+    if check:
+        _check(st, "p3_batch_ftran_r2c")
+    return st
+
+
+def p3_batch_btran_c2r(batch, ins, outs, wss, stream, check=True):
+    st = load().p3_batch_btran_c2r(batch, None if ins is None else _ptrs(ins), None if outs is None else _ptrs(outs),
+                                   None if wss is None else _ptrs(wss), stream)
+    if check:
+        _check(st, "p3_batch_btran_c2r")
     return st
 
 
@@ -343,3 +382,43 @@ class Plan:
         ws = self.workspace() if ws is None else ws
         self._call(p3_btran_c2r, X, out, ws, stream)
         return out
+
+
+class Batch:
+    """Independent plans run side by side on `nstreams` internal streams
+    (p3_batch_*): forward(xs) / backward(Xs) take one tensor per plan."""
+
+    def __init__(self, plans, nstreams=8):
+        self.plans = list(plans)
+        self.torch = self.plans[0].torch
+        _, self.handle = p3_batch_create([p.handle for p in self.plans], nstreams)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            p3_batch_destroy(h)
+            self.handle = None
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.plans[0].device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def forward(self, xs, outs=None, stream=None):
+        outs = [p.empty_complex() for p in self.plans] if outs is None else outs
+        for p, x, o in zip(self.plans, xs, outs):
+            p._check_tensor(x, p.real_shape, p.real_dtype, "input")
+            p._check_tensor(o, p.complex_shape, p.complex_dtype, "output")
+        wss = [p.workspace() for p in self.plans]
+        p3_batch_ftran_r2c(self.handle, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs],
+                           [0 if w is None else w.data_ptr() for w in wss], self._stream(stream))
+        return outs
+
+    def backward(self, Xs, outs=None, stream=None):
+        outs = [p.empty_real() for p in self.plans] if outs is None else outs
+        for p, X, o in zip(self.plans, Xs, outs):
+            p._check_tensor(X, p.complex_shape, p.complex_dtype, "input")
+            p._check_tensor(o, p.real_shape, p.real_dtype, "output")
+        wss = [p.workspace() for p in self.plans]
+        p3_batch_btran_c2r(self.handle, [X.data_ptr() for X in Xs], [o.data_ptr() for o in outs],
+                           [0 if w is None else w.data_ptr() for w in wss], self._stream(stream))
+        return outs

@@ -111,6 +111,13 @@ def test_null_plan_calls(lib):
     assert P.p3_plan_wait_status(None) == P.P3_ERR_INVALID
     assert P.p3_plan_set_wait_limits(None, 10, 0, check=False) == P.P3_ERR_INVALID
     assert P.p3_plan_set_fused_lag(None, 1, check=False) == P.P3_ERR_INVALID
+    st, h = P.p3_batch_create(None, 2, check=False)
+    assert st == P.P3_ERR_INVALID and h is None
+    st, h = P.p3_batch_create([None], 2, check=False)
+    assert st == P.P3_ERR_INVALID and h is None
+    assert P.p3_batch_destroy(None) == P.P3_OK
+    assert P.p3_batch_ftran_r2c(None, None, None, None, None, check=False) == P.P3_ERR_INVALID
+    assert P.p3_batch_btran_c2r(None, None, None, None, None, check=False) == P.P3_ERR_INVALID
 
 
 def test_binding_raises_when_library_missing(tmp_path, monkeypatch):
