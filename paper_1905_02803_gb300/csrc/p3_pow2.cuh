@@ -679,8 +679,11 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     typedef P2<N, E> PL;
     constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL;
     constexpr int M = N / 2;
-    constexpr int LD = B + 1;  // result tile: element e of line l at e * LD + l
-    static_assert(NT % B == 0, "store lanes keep their line");
+    // result tile: element e of line l at e * B + (l ^ sw(e)); the swizzle
+    // spreads a warp's writes (one line, consecutive e) and keeps the store
+    // phase's reads (B lines of consecutive e) on distinct banks
+    constexpr int SWS = B >= 16 ? 0 : B == 8 ? 1 : 2;
+    static_assert(NT % B == 0 && B >= 4, "store lanes keep their line");
     typedef RowSlot<N, E> S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
@@ -718,7 +721,10 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 #pragma unroll
         for (int b = 0; b < PLast::BM; ++b)
 #pragma unroll
-            for (int r = 0; r < PLast::R; ++r) s[(u + PLast::out_K(b, r)) * LD + l] = v[b * PLast::R + r];
+            for (int r = 0; r < PLast::R; ++r) {
+                const int e = u + PLast::out_K(b, r);
+                s[e * B + (l ^ ((e >> SWS) & (B - 1)))] = v[b * PLast::R + r];
+            }
     }
     __syncthreads();
     constexpr int NOUT = DCT ? M + 1 : DST ? M - 1 : N;
@@ -728,7 +734,8 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         C* dst = static_cast<C*>(a.dst) + lbase(a.out, LL);
         const long long es = a.out.es;
         for (int c = tid / B; c < NOUT; c += NT / B) {
-            C x = s[(DST ? c + 1 : c) * LD + ll];
+            const int e = DST ? c + 1 : c;
+            C x = s[e * B + (ll ^ ((e >> SWS) & (B - 1)))];
             if constexpr (DST) x = mk<C>(-x.y, x.x);
             else if constexpr (INV) x = swp(x);
             dst[(long long)c * es] = x;
@@ -739,7 +746,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 template <typename T, int N, int E, int B> __host__ __device__ constexpr size_t zrow_smem()
 {
     typedef typename CxT<T>::t C;
-    const size_t ex = (size_t)B * (size_t)RowSlot<N, E>::RP, res = (size_t)N * (size_t)(B + 1);
+    const size_t ex = (size_t)B * (size_t)RowSlot<N, E>::RP, res = (size_t)N * (size_t)B;
     return (ex > res ? ex : res) * sizeof(C);
 }
 
