@@ -127,6 +127,7 @@ struct PlaneArgs {
     int lag;              // consumers of plane p follow the producers of plane p + lag (1 <= lag <= nplanes)
     int grid;             // persistent CTAs
     int nt;               // threads per CTA
+    int tp;               // 1: planes stored transposed, [x][y] (y fastest)
     int bx, by;           // rows per X tile, lines per Y tile
     size_t smem;
     int kx, ky;           // row / column line lengths (complex points)
@@ -134,7 +135,7 @@ struct PlaneArgs {
 
 // Returns true when a plane-fused kernel exists for these X and Y stages;
 // fills f (except buffers and counters).
-bool fused_configure(PlaneArgs& f, const StageArgs& x, const StageArgs& y, int dir, size_t csize);
+bool fused_configure(PlaneArgs& f, const StageArgs& x, const StageArgs& y, int dir, size_t csize, bool tp);
 cudaError_t fused_prepare();
 cudaError_t fused_launch(const PlaneArgs& f, cudaStream_t s);
 

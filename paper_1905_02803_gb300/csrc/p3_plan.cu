@@ -568,7 +568,24 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         const Stage& sx = d == 0 ? s0 : s1;
         const Stage& sy = d == 0 ? s1 : s0;
         if (sy.src != sy.dst || (d == 0 ? sx.dst != sy.src : sx.src != sy.dst)) continue;
-        if (p3::fused_configure(fcfg[d], sx.a, sy.a, d == 0 ? 0 : 1, P->csize)) fuse_at[d] = i;
+        // with the ZYX layout the planes between the stages live only in the
+        // workspace, so they are stored transposed ([x][y]: contiguous Y
+        // lines); the Z stage of the direction addresses them that way
+        const bool tp = zyx && d < 2 && ttype[2] != P3_EMPTY;
+        if (!p3::fused_configure(fcfg[d], sx.a, sy.a, d == 0 ? 0 : 1, P->csize, tp)) continue;
+        fuse_at[d] = i;
+        if (tp) {
+            const LineMap ws_lines = LineMap{H * NY, 0, 1, H * NY};  // line x * Ny + y of planes [x][y]
+            const LineMap zyx_lines = LineMap{H * NY, 0, NZ, 1};    // the same line in ZYX order
+            Stage& z = d == 0 ? v[2] : v[0];
+            if (d == 0) {
+                z.a.in = ws_lines;
+                z.a.out = zyx_lines;
+            } else {
+                z.a.in = zyx_lines;
+                z.a.out = ws_lines;
+            }
+        }
     }
     const bool any_fused = fuse_at[0] >= 0 || fuse_at[1] >= 0 || fuse_at[2] >= 0;
     bool need_ws = false;
