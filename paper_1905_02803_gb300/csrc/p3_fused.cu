@@ -219,12 +219,13 @@ __host__ __device__ constexpr size_t fused_smem()
     return row > col ? row : col;
 }
 
-// Threads per CTA of each direction's fused kernel.
-#ifndef P3_FUSED_NT_FWD
-#define P3_FUSED_NT_FWD 256
+// Threads per CTA of the fused kernels: four 128-thread CTAs per SM with
+// transposed planes (measured faster than two of 256), two of 256 otherwise.
+#ifndef P3_FUSED_NT
+#define P3_FUSED_NT 256
 #endif
-#ifndef P3_FUSED_NT_INV
-#define P3_FUSED_NT_INV 256
+#ifndef P3_FUSED_NT_TP
+#define P3_FUSED_NT_TP 128
 #endif
 
 // NX: half length of the real X rows (complex points), NY: Y line length,
@@ -341,10 +342,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) plane_kernel(const __grid_consta
 template <int NX, int NY> void* pick_dir(int dir, bool tp)
 {
     if (tp)
-        return dir == 0 ? (void*)plane_kernel<float, NX, NY, 0, P3_FUSED_NT_FWD, true>
-                        : (void*)plane_kernel<float, NX, NY, 1, P3_FUSED_NT_INV, true>;
-    return dir == 0 ? (void*)plane_kernel<float, NX, NY, 0, P3_FUSED_NT_FWD, false>
-                    : (void*)plane_kernel<float, NX, NY, 1, P3_FUSED_NT_INV, false>;
+        return dir == 0 ? (void*)plane_kernel<float, NX, NY, 0, P3_FUSED_NT_TP, true>
+                        : (void*)plane_kernel<float, NX, NY, 1, P3_FUSED_NT_TP, true>;
+    return dir == 0 ? (void*)plane_kernel<float, NX, NY, 0, P3_FUSED_NT, false>
+                    : (void*)plane_kernel<float, NX, NY, 1, P3_FUSED_NT, false>;
 }
 template <int NX> void* pick_ny(int ny, int dir, bool tp)
 {
@@ -386,11 +387,8 @@ bool fused_configure(PlaneArgs& f, const StageArgs& x, const StageArgs& y, int d
         return false;
     void* fn = pick(x.nfft, y.nfft, dir, tp);
     if (!fn) return false;
-    const int nt = dir == 0 ? P3_FUSED_NT_FWD : P3_FUSED_NT_INV;
-    const size_t smem = dir == 0 ? (tp ? smem_nt<P3_FUSED_NT_FWD, true>(x.nfft, y.nfft)
-                                       : smem_nt<P3_FUSED_NT_FWD, false>(x.nfft, y.nfft))
-                                 : (tp ? smem_nt<P3_FUSED_NT_INV, true>(x.nfft, y.nfft)
-                                       : smem_nt<P3_FUSED_NT_INV, false>(x.nfft, y.nfft));
+    const int nt = tp ? P3_FUSED_NT_TP : P3_FUSED_NT;
+    const size_t smem = tp ? smem_nt<P3_FUSED_NT_TP, true>(x.nfft, y.nfft) : smem_nt<P3_FUSED_NT, false>(x.nfft, y.nfft);
     int dev = 0, sms = 0, coop = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
         cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
@@ -413,6 +411,7 @@ bool fused_configure(PlaneArgs& f, const StageArgs& x, const StageArgs& y, int d
     f.tp = tp ? 1 : 0;
     f.bx = fx_B<float>(x.nfft, nt);
     f.by = tp ? fl_B<float>(y.nfft, nt) : fy_B<float>(y.nfft, nt);
+    if (y.nfft % f.bx) return false;  // X tiles of transposed planes are whole
     f.grid = per_sm * sms;
     f.spin_limit = 1u << 23;
     f.lag = 1;
