@@ -36,19 +36,28 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 template <int B> __device__ __forceinline__ int tsw(int k) { return (k >> (B >= 16 ? 0 : B == 8 ? 1 : 2)) & (B - 1); }
 
 // X r2c of rows y0 .. y0 + B - 1 of one plane (real rows L0 + l of the X
-// stage's input), written to plane[k * ny + y0 + l].
+// stage's input), written to plane[k * ny + y0 + l].  The rows' last-pass
+// outputs go to shared memory once; the store lanes (across rows) read
+// Z[k] and Z[N-k] there and write the post-twiddled F[k] straight to the
+// plane.  Row pitch RPX = 4 (mod 16) complex keeps those cross-row reads on
+// distinct banks.
+template <int N, int E> __host__ __device__ constexpr int xt_pitch()
+{
+    return (N + N / E) + ((4 - (N + N / E) % 16) + 16) % 16;
+}
+
 template <typename T, int N, int E, int B, int LP>
 __device__ __forceinline__ void xr2c_tile_t(const StageArgs& a, long long L0, typename CxT<T>::t* plane, int y0,
                                             int ny, typename CxT<T>::t* s)
 {
     typedef typename CxT<T>::t C;
     typedef P2<N, E> PL;
-    constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL, KPT = N / TPL + 1;
+    constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL, RPX = xt_pitch<N, E>();
     typedef RowSlot<N, E> S;
     const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
     const long long L = L0 + l;
     const C* tw2 = static_cast<const C*>(a.tw2);
-    C* srow = s + l * S::RP;
+    C* srow = s + l * RPX;
     C v[E];
     typedef PassIdx<N, E, 0> P0;
     typedef PassIdx<N, E, NP - 1> PLast;
@@ -69,30 +78,18 @@ __device__ __forceinline__ void xr2c_tile_t(const StageArgs& a, long long L0, ty
 #pragma unroll
             for (int r = 0; r < PLast::R; ++r) srow[S::at_k(u, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
     }
-    row_sync<TPL>();
-    // F[k] = (Z[k] + conj Z[N-k]) / 2 - i exp(-2 pi i k / 2N) (Z[k] - conj Z[N-k]) / 2, k = t + j TPL
-    C F[KPT];
-#pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int k = t + j * TPL;
-        if (k <= N) {
-            const C zk = srow[S::at(k == N ? 0 : k)];
-            const C zm = cnj(srow[S::at(k == 0 ? 0 : N - k)]);
-            const C p = mul(ldg(tw2 + k), sub(zk, zm));
-            F[j] = mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x));
-        }
-    }
-    __syncthreads();  // the transposed tile overlaps other rows' exchange rows
-#pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int k = t + j * TPL;
-        if (k <= N) s[k * B + (l ^ tsw<B>(k))] = F[j];
-    }
-    __syncthreads();
+    __syncthreads();  // the store lanes read every row of the tile
+    // F[k] = (Z[k] + conj Z[N-k]) / 2 - i exp(-2 pi i k / 2N) (Z[k] - conj Z[N-k]) / 2
     static_assert(NT % B == 0, "store lanes keep their row");
     const int ll = tid % B;
+    const C* zr = s + ll * RPX;
     C* dst = plane + y0 + ll;
-    for (int k = tid / B; k <= N; k += NT / B) dst[(long long)k * ny] = s[k * B + (ll ^ tsw<B>(k))];
+    for (int k = tid / B; k <= N; k += NT / B) {
+        const C zk = zr[S::at(k == N ? 0 : k)];
+        const C zm = cnj(zr[S::at(k == 0 ? 0 : N - k)]);
+        const C p = mul(ldg(tw2 + k), sub(zk, zm));
+        dst[(long long)k * ny] = mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x));
+    }
 }
 
 // X c2r of rows y0 .. y0 + B - 1 of one plane, read from plane[k * ny + y0 + l]
@@ -214,6 +211,8 @@ __host__ __device__ constexpr size_t fused_smem()
     const size_t bx = (size_t)fx_B<T>(NX, NT);
     size_t row = bx * (size_t)(NX + NX / fx_E<T>(NX) + 1) * sizeof(C);
     if (TP && bx * (size_t)(NX + 1) * sizeof(C) > row) row = bx * (size_t)(NX + 1) * sizeof(C);
+    if (TP && bx * (size_t)xt_pitch<NX, fx_E<T>(NX)>() * sizeof(C) > row)
+        row = bx * (size_t)xt_pitch<NX, fx_E<T>(NX)>() * sizeof(C);
     const size_t col = TP ? (size_t)fl_B<T>(NY, NT) * (size_t)(NY + NY / fl_E<T>(NY) + 1) * sizeof(C)
                           : (size_t)fy_B<T>(NY, NT) * (size_t)col_smem_slots<T, NY>() * sizeof(C);
     return row > col ? row : col;
