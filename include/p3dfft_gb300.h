@@ -82,6 +82,7 @@ typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2, P3_SINE = 3 } p3_ttype;
 #define P3_FLAG_TC_SPLIT 1u
 #define P3_FLAG_PADDED_REAL 2u
 #define P3_FLAG_NO_FUSE 4u
+#define P3_FLAG_TUNE 8u
 
 /* Table 1: storage order of the Z-pencil complex array. */
 typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
@@ -116,6 +117,13 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                so the second stage reads the first one's output from L2.
  *                Its CTAs wait on one another with bounded waits; see
  *                p3_plan_wait_status().
+ *              P3_FLAG_TUNE: for each direction with a plane-fused launch,
+ *                time the fused launch at a few queue lags and the separate
+ *                X and Y launches once, here, and keep the fastest (all give
+ *                the same result).  Allocates two buffers of the transform's
+ *                size plus a workspace for the duration of the call, so plan
+ *                creation takes milliseconds to a second; the timings appear
+ *                in p3_plan_describe().
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.

@@ -17,6 +17,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <complex>
 #include <map>
 #include <new>
@@ -344,6 +345,98 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb)
 }  // namespace
 
 extern "C" {
+static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, void* stream);
+}
+
+// P3_FLAG_TUNE: for each direction with a plane-fused launch, time the
+// candidates -- the fused launch at a few queue lags and the separate X and
+// Y launches (with plain planes) -- on temporary buffers of the transform's
+// size, and keep the fastest.  The candidates compute the same result.
+static p3_status tune(p3_plan P, std::vector<Stage> (&unfused)[3], std::string& report)
+{
+    const size_t rowr = P->padded ? 2 * (size_t)P->H : (size_t)P->nx;
+    const size_t nreal = rowr * P->ny * P->nz * (P->csize / 2);
+    const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
+    const size_t nbuf = nreal > ncplx ? nreal : ncplx;
+    void *a = NULL, *b = NULL, *w = NULL;
+    cudaStream_t st = NULL;
+    cudaEvent_t e0 = NULL, e1 = NULL;
+    p3_status rc = P3_OK;
+    if (cudaMalloc(&a, nbuf) != cudaSuccess || cudaMalloc(&b, nbuf) != cudaSuccess ||
+        cudaMalloc(&w, P->ws_bytes) != cudaSuccess)
+        rc = P3_ERR_NOMEM;
+    if (rc == P3_OK && (cudaMemset(a, 0x3c, nbuf) != cudaSuccess ||
+                        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = P3_ERR_CUDA;
+    const bool timing = P->timing;
+    P->timing = false;
+    for (int d = 0; d < 2 && rc == P3_OK; ++d) {
+        int fi = -1;
+        for (size_t i = 0; i < P->st[d].size(); ++i)
+            if (P->st[d][i].fused) fi = (int)i;
+        if (fi < 0) continue;
+        const std::vector<Stage> fused = P->st[d];
+        const int lag0 = fused[(size_t)fi].f.lag, np = fused[(size_t)fi].f.nplanes;
+        std::vector<int> lags;  // 0: separate X and Y launches
+        for (int L : {lag0, lag0 / 2, (3 * lag0) / 2, 2 * lag0}) {
+            const int l = L < 1 ? 1 : (L > np ? np : L);
+            if (std::find(lags.begin(), lags.end(), l) == lags.end()) lags.push_back(l);
+        }
+        lags.push_back(0);
+        float best = 1e30f;
+        int pick = lag0;
+        std::string line = std::string(d == 0 ? "fwd" : "bwd") + " tuned:";
+        for (int L : lags) {
+            if (L == 0) {
+                P->st[d] = unfused[d];
+            } else {
+                P->st[d] = fused;
+                P->st[d][(size_t)fi].f.lag = L;
+            }
+            const void* in = d == 0 ? a : b;
+            void* out = d == 0 ? b : a;
+            float ms = 0.f;
+            for (int rep = 0; rep < 4 && rc == P3_OK; ++rep) {
+                if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = P3_ERR_CUDA;
+                if (rc == P3_OK) rc = run(P, d, in, out, w, st);
+            }
+            if (rc == P3_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = P3_ERR_CUDA;
+            if (rc != P3_OK) break;
+            ms /= 3.f;
+            char buf[64];
+            snprintf(buf, sizeof(buf), " %s=%.3fms", L ? ("lag" + std::to_string(L)).c_str() : "separate", ms);
+            line += buf;
+            if (ms < best) {
+                best = ms;
+                pick = L;
+            }
+        }
+        if (rc != P3_OK) break;
+        if (pick == 0) {
+            P->st[d] = unfused[d];
+        } else {
+            P->st[d] = fused;
+            P->st[d][(size_t)fi].f.lag = pick;
+            P->fused_lag_default[d] = pick;
+        }
+        report += line + " -> " + (pick ? "lag" + std::to_string(pick) : std::string("separate")) + "\n";
+    }
+    P->timing = timing;
+    if (rc == P3_OK && p3_plan_wait_status(P) != P3_OK) rc = P3_ERR_TIMEOUT;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (w) cudaFree(w);
+    cudaGetLastError();
+    return rc;
+}
+
+extern "C" {
 
 const char* p3_status_string(p3_status s)
 {
@@ -368,7 +461,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     if (!out) return P3_ERR_INVALID;
     *out = NULL;
     if (!ttype || nx < 1 || ny < 1 || nz < 1 ||
-        (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL | P3_FLAG_NO_FUSE)))
+        (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL | P3_FLAG_NO_FUSE | P3_FLAG_TUNE)))
         return P3_ERR_INVALID;
     if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
     if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
@@ -553,6 +646,9 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         delete P;
         return rc;
     }
+    // the stage lists before fusion (separate X and Y launches, plain
+    // planes): the autotuner's other candidate
+    std::vector<Stage> unfused[3] = {P->st[0], P->st[1], P->st[2]};
     // ---- plane-fused X + Y launches ----------------------------------------
     // fwd: stages 0 (X, src -> work) and 1 (Y in place on work); inverse and
     // hook-mode inverse: stages 1 (Y in place on work) and 2 (X, work -> out)
@@ -646,6 +742,12 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.chirp = resolve(pd.chirp);
             a.bhat = resolve(pd.bhat);
             a.twm = resolve(pd.twm);
+            StageArgs& b = unfused[d][i].a;
+            b.tw = a.tw;
+            b.tw2 = a.tw2;
+            b.chirp = a.chirp;
+            b.bhat = a.bhat;
+            b.twm = a.twm;
         }
     }
     for (int d = 0; d < 3; ++d) {
@@ -702,6 +804,18 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             return P3_ERR_NOMEM;
         }
     }
+    // ---- autotuning (P3_FLAG_TUNE) -------------------------------------------
+    std::string tuned;
+    if ((flags & P3_FLAG_TUNE) && any_fused) {
+        rc = tune(P, unfused, tuned);
+        if (rc != P3_OK) {
+            if (P->dtab) cudaFree(P->dtab);
+            if (P->derr) cudaFree(P->derr);
+            cudaGetLastError();
+            delete P;
+            return rc;
+        }
+    }
     // ---- description ----------------------------------------------------------
     char line[512];
     for (int d = 0; d < 2; ++d) {
@@ -750,6 +864,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             P->desc += line;
         }
     }
+    if (!tuned.empty()) P->desc += tuned;
     if (!P->st[2].empty()) {
         std::string names;
         for (auto& s : P->st[2]) names += (names.empty() ? "" : ",") + std::string(s.name);

@@ -102,3 +102,23 @@ def test_fused_lag_keeps_results(lag):
     torch.cuda.synchronize()
     assert torch.equal(Xf, Xs) and torch.equal(yf, ys)
     assert P.p3_plan_wait_status(pf.handle) == P.P3_OK
+
+
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_tuned_plan_keeps_results(layout):
+    """P3_FLAG_TUNE times the fused launch at a few lags and the separate
+    stages, keeps the fastest per direction; every candidate computes the
+    same arithmetic, so the result equals the separate-stage plan's."""
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = 512, 256, 24
+    pt = P.Plan(nx, ny, nz, precision="f32", layout=layout, flags=P.P3_FLAG_TUNE)
+    ps = P.Plan(nx, ny, nz, precision="f32", layout=layout, flags=P.P3_FLAG_NO_FUSE)
+    d = pt.describe()
+    assert "fwd tuned:" in d and "bwd tuned:" in d and "separate=" in d, d
+    x = torch.from_numpy(inputs.uniform_field((nz, ny, nx), 21)).to("cuda", torch.float32)
+    Xt, Xs = pt.forward(x), ps.forward(x)
+    yt, ys = pt.backward(Xt), ps.backward(Xs)
+    torch.cuda.synchronize()
+    assert torch.equal(Xt, Xs) and torch.equal(yt, ys)
+    assert P.p3_plan_wait_status(pt.handle) == P.P3_OK
