@@ -83,6 +83,7 @@ typedef enum { P3_FFT = 0, P3_CHEB = 1, P3_EMPTY = 2, P3_SINE = 3 } p3_ttype;
 #define P3_FLAG_PADDED_REAL 2u
 #define P3_FLAG_NO_FUSE 4u
 #define P3_FLAG_TUNE 8u
+#define P3_FLAG_NO_TMA 16u
 
 /* Table 1: storage order of the Z-pencil complex array. */
 typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
@@ -124,6 +125,9 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                size plus a workspace for the duration of the call, so plan
  *                creation takes milliseconds to a second; the timings appear
  *                in p3_plan_describe().
+ *              P3_FLAG_NO_TMA: load the forward ZYX-store Z stage's input
+ *                tiles with ordinary loads instead of tensor-memory-access
+ *                (TMA) copies (FP32 Z lines of 256 .. 2048 points).
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.
@@ -200,6 +204,8 @@ p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
  * and lets the launch finish.  p3_plan_wait_status() synchronises with the
  * device, returns P3_ERR_TIMEOUT if any wait of this plan gave up since the
  * last check (and clears the mark), else P3_OK; P3_ERR_INVALID for NULL.
+ * The waits of the TMA-staged Z kernels (for their tensor copies) report the
+ * same way.
  */
 p3_status p3_plan_wait_status(p3_plan plan);
 

@@ -2,6 +2,7 @@
 // kernels (p3_kernels.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -48,6 +49,10 @@ enum StageOp : int {
 
 // Everything one stage kernel launch needs (passed by value).
 struct StageArgs {
+    // TMA descriptor of the input tile (tma = 1): lines as the inner
+    // dimension, line elements as the outer one; encoded per call with the
+    // call's source pointer
+    CUtensorMap tmap;
     const void* src;
     void* dst;
     LineMap in, out;
@@ -89,6 +94,10 @@ struct StageArgs {
     int persist;
     // 1: tensor-core split-precision kernel (p3_tc.cu)
     int tc;
+    // 1: TMA-staged ZYX-store column kernel (input tile by tensor copies)
+    int tma;
+    // status word of the plan: a bounded device wait that gave up ORs a bit in
+    unsigned* err;
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.
@@ -99,7 +108,9 @@ cudaError_t prepare_kernels();
 
 // Power-of-two specialised kernels (p3_pow2.cu): configure a stage for them
 // (returns false when none applies), set them up, launch one stage.
-bool pow2_configure(StageArgs& a, size_t csize);
+bool pow2_configure(StageArgs& a, size_t csize, bool allow_tma);
+// Encodes a.tmap for a stage with a.tma set, from a.src (p3_pow2.cu).
+cudaError_t pow2_encode_tma(StageArgs& a);
 cudaError_t pow2_prepare();
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t s);
 

@@ -292,7 +292,7 @@ void tile_setup(StageArgs& a, size_t csize, unsigned flags)
     a.smem = 2 * (size_t)len * (size_t)a.LDB * csize;  // ping-pong buffers
     a.kern = p3::KIND_GENERIC;
     a.tc = 0;
-    p3::pow2_configure(a, csize);
+    p3::pow2_configure(a, csize, !(flags & P3_FLAG_NO_TMA));
     if (flags & P3_FLAG_TC_SPLIT) p3::tc_configure(a, csize);
 }
 
@@ -312,9 +312,10 @@ const char* op_name(int op)
     }
 }
 
-const char* kern_name(int k, int tc)
+const char* kern_name(int k, int tc, int tma = 0)
 {
     if (tc) return "tc_split_col";
+    if (tma) return "pow2_col_zyx_store_tma";
     switch (k) {
     case p3::KIND_COL_DD: return "pow2_col";
     case p3::KIND_COL_DS: return "pow2_col_zyx_store";
@@ -461,7 +462,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     if (!out) return P3_ERR_INVALID;
     *out = NULL;
     if (!ttype || nx < 1 || ny < 1 || nz < 1 ||
-        (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL | P3_FLAG_NO_FUSE | P3_FLAG_TUNE)))
+        (flags & ~(unsigned)(P3_FLAG_TC_SPLIT | P3_FLAG_PADDED_REAL | P3_FLAG_NO_FUSE | P3_FLAG_TUNE |
+                             P3_FLAG_NO_TMA)))
         return P3_ERR_INVALID;
     if (prec != P3_F32 && prec != P3_F64) return P3_ERR_INVALID;
     if (out_layout != P3_LAYOUT_ZYX && out_layout != P3_LAYOUT_XYZ) return P3_ERR_INVALID;
@@ -793,7 +795,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         v.erase(v.begin() + i, v.begin() + i + 2);
         v.insert(v.begin() + i, m);
     }
-    if (any_fused) {
+    {  // the plan's device status word (bounded waits of fused and TMA kernels)
         cudaError_t ce = cudaMalloc(&P->derr, 256);
         if (ce == cudaSuccess) ce = cudaMemset(P->derr, 0, 256);
         if (ce != cudaSuccess) {
@@ -858,7 +860,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             snprintf(line, sizeof(line),
                      "%s %s kernel=%s op=%s nfft=%d%s radices=%s lines=%lld B=%d LDB=%d tpl=%d threads=%d "
                      "smem=%zu bytes=%.0f\n",
-                     d == 0 ? "fwd" : "bwd", s.name, kern_name(a.kern, a.tc), op_name(a.op), a.nfft,
+                     d == 0 ? "fwd" : "bwd", s.name, kern_name(a.kern, a.tc, a.tma), op_name(a.op), a.nfft,
                      a.blue ? (" bluestein_m=" + std::to_string(a.m)).c_str() : "", rs.c_str(), a.nlines, a.B,
                      a.LDB, a.tpl, a.threads, a.smem, s.bytes);
             P->desc += line;
@@ -946,6 +948,7 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
         StageArgs a = st.a;
         a.src = bufs[st.src];
         a.dst = bufs[st.dst];
+        a.err = P->derr;
         cudaError_t e;
         if (st.fused) {
             p3::PlaneArgs f = st.f;
@@ -960,7 +963,8 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
             f.extra = P->wait_extra;
             e = p3::fused_launch(f, s);
         } else {
-            e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
+            e = a.tma ? p3::pow2_encode_tma(a) : cudaSuccess;
+            if (e == cudaSuccess) e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
         }
         if (e != cudaSuccess) return P3_ERR_CUDA;
         ++i;

@@ -1,6 +1,8 @@
 // Configuration, set-up and launch of the power-of-two stage kernels
 // (templates in p3_pow2.cuh, instantiated per precision in p3_pow2_f32.cu and
 // p3_pow2_f64.cu).
+#include <cudaTypedefs.h>
+
 #include "p3_internal.h"
 
 namespace p3 {
@@ -10,6 +12,9 @@ void* pow2_pick_f64(int kind, int N, bool inv, int sym, bool pl);
 void pow2_shape_f32(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
 void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
 
+void* pow2_pick_tma_f32(int N, int sym);
+size_t pow2_tma_smem_f32(int N, int sym);
+
 // Column-kernel symmetry variant of a stage: 0 plain, 1 DCT-I, 2 DST-I.
 static int sym_of(const StageArgs& a) { return a.op == OP_DCT1 ? 1 : a.op == OP_DST1 ? 2 : 0; }
 
@@ -17,17 +22,17 @@ namespace {
 bool is_pow2_in_range(int n) { return n >= 64 && n <= 4096 && (n & (n - 1)) == 0; }
 }  // namespace
 
-static bool configure(StageArgs& a, size_t csize);
+static bool configure(StageArgs& a, size_t csize, bool allow_tma);
 
-bool pow2_configure(StageArgs& a, size_t csize)
+bool pow2_configure(StageArgs& a, size_t csize, bool allow_tma)
 {
     StageArgs b = a;  // a keeps its generic configuration unless this succeeds
-    if (!configure(b, csize)) return false;
+    if (!configure(b, csize, allow_tma)) return false;
     a = b;
     return true;
 }
 
-static bool configure(StageArgs& a, size_t csize)
+static bool configure(StageArgs& a, size_t csize, bool allow_tma)
 {
     if (a.blue) return false;
     const int N = a.nfft;
@@ -59,6 +64,15 @@ static bool configure(StageArgs& a, size_t csize)
     a.smem = smem;
     a.kern = kind;
     a.persist = 0;
+    a.tma = 0;
+    // TMA-staged input tile for the forward ZYX store: the tile's lines must
+    // be adjacent (the tensor's inner dimension) and their elements a
+    // 16-byte multiple apart, past the last line
+    if (f32 && allow_tma && kind == KIND_COL_DS && !pl && N >= 256 && N <= 2048 && a.in.lstride == 1 &&
+        a.in.per >= a.nlines && a.in.es % 2 == 0 && a.in.es >= a.nlines && a.gcount == 0 && (B % 2) == 0) {
+        a.tma = 1;
+        a.smem = pow2_tma_smem_f32(N, sym_of(a));
+    }
     if (pl) {
         // persistent grid: resident CTAs per SM times the SM count
         void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, sym_of(a), true)
@@ -86,6 +100,12 @@ cudaError_t pow2_prepare()
                     for (int sym = 0; sym < 3; ++sym)
                         for (int pl = 0; pl < 2; ++pl) {
                             void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, sym, pl) : pow2_pick_f64(kind, N, inv, sym, pl);
+                            if (f == 0 && kind == KIND_COL_DS && !inv && !pl) {
+                                void* ft = pow2_pick_tma_f32(N, sym);
+                                if (ft && cudaFuncSetAttribute(ft, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               227 * 1024) != cudaSuccess)
+                                    return cudaGetLastError();
+                            }
                             if (!fn) continue;
                             cudaError_t e =
                                 cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -98,7 +118,8 @@ cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
 {
     const bool inv = a.sign > 0, pl = a.persist > 0;
     const int sym = sym_of(a);
-    void* fn = f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym, pl) : pow2_pick_f64(a.kern, a.nfft, inv, sym, pl);
+    void* fn = a.tma ? pow2_pick_tma_f32(a.nfft, sym)
+                     : (f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym, pl) : pow2_pick_f64(a.kern, a.nfft, inv, sym, pl));
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;
     long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;
@@ -106,6 +127,38 @@ cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<StageArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(a.threads), args, a.smem, st);
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (resolved once)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+cudaError_t pow2_encode_tma(StageArgs& a)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // 8-byte complex elements: lines (inner, unit stride) x line elements (outer, es apart)
+    const cuuint64_t dims[2] = {(cuuint64_t)a.nlines, (cuuint64_t)a.n_in};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.in.es * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)a.B, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(a.src), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace p3

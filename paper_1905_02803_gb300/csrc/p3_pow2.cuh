@@ -359,6 +359,153 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 }
 
 // ---------------------------------------------------------------------------
+// ZYX-store column kernel with a TMA-staged input tile (forward Z stage).
+// The tile's B lines are adjacent in memory and their elements es apart, so
+// the tile is a 2D box of the array (lines inner, elements outer): one thread
+// arms an mbarrier with the tile's byte count and issues the tensor copies
+// (boxes of B x 256 into a dense [e][l] tile); the CTA waits on the barrier
+// (bounded), takes the first pass from shared memory and continues as the
+// column kernel's ZYX-store form.  A wait that gives up sets bit 2 of
+// *a.err, waits (bounded) for the copies in flight and leaves the tile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+constexpr unsigned kTmaSpin = 1u << 22;  // try_wait polls before a wait gives up
+constexpr int kTmaRows = 256;            // box height (elements of a line)
+
+template <int N, int SYM> __host__ __device__ constexpr int tma_rows()
+{
+    return SYM == 1 ? N / 2 + 1 : SYM == 2 ? N / 2 - 1 : N;
+}
+template <typename T, int N, int B, int SYM> __host__ __device__ constexpr size_t tma_tile_bytes()
+{
+    return (size_t)((tma_rows<N, SYM>() + kTmaRows - 1) / kTmaRows) * kTmaRows * B * 2 * sizeof(T);
+}
+
+template <typename T, int N, int E, int B, int SYM>
+__global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
+    col_kernel_tma(const __grid_constant__ StageArgs a)
+{
+    static_assert(sizeof(T) == 4, "TMA tiles of 8-byte complex elements");
+    constexpr bool DCT = SYM == 1, DST = SYM == 2;
+    typedef typename CxT<T>::t C;
+    typedef P2<N, E> PL;
+    constexpr int NP = PL::NPASS;
+    typedef ColSlot<T, B, true> S;
+    typedef EF<T, N, E, B> Ef;
+    constexpr int M = N / 2;
+    constexpr int NBOX = (tma_rows<N, SYM>() + kTmaRows - 1) / kTmaRows;
+    constexpr unsigned TX = (unsigned)tma_tile_bytes<T, N, B, SYM>();
+    constexpr size_t SLOTS = (size_t)col_smem_slots<T, N>() * B * sizeof(C);
+    constexpr size_t AREA = SLOTS > TX ? SLOTS : TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 128-byte aligned tile (the dynamic block is requested 128 + 16 bytes larger)
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    C* s = reinterpret_cast<C*>(base);
+    const unsigned bar = smem_u32(base + AREA);
+    const int tid = threadIdx.x, l = tid % B, t = tid / B;
+    const long long L0 = (long long)blockIdx.x * B;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(TX) : "memory");
+#pragma unroll
+        for (int k = 0; k < NBOX; ++k)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(smem_u32(s + (size_t)k * kTmaRows * B)),
+                "l"(reinterpret_cast<unsigned long long>(&a.tmap)), "r"((int)L0), "r"(k * kTmaRows), "r"(bar)
+                : "memory");
+    }
+    int ok = 0;
+    for (unsigned it = 0; it < kTmaSpin; ++it)
+        if (mbar_try_wait(bar, 0)) {
+            ok = 1;
+            break;
+        }
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(a.err, 2u);
+        for (unsigned it = 0; it < kTmaSpin && !mbar_try_wait(bar, 0); ++it) {
+        }
+        return;
+    }
+    const C zero = mk<C>((T)0, (T)0);
+    const C* tw = static_cast<const C*>(a.tw);
+    C v[E];
+    typedef PassIdx<N, E, 0> P0;
+#pragma unroll
+    for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+        for (int r = 0; r < P0::R; ++r) {
+            const int e = t + P0::in_K(b, r);
+            C x;
+            if constexpr (DST) {
+                x = (e != 0 && e != M) ? s[(e < M ? e - 1 : N - 1 - e) * B + l] : zero;
+                if (e > M) x = mk<C>(-x.x, -x.y);
+            } else {
+                x = s[(DCT ? (e <= M ? e : N - e) : e) * B + l];
+            }
+            v[b * P0::R + r] = x;
+        }
+    pass_compute<C, T, N, E, 0>(v, t, tw, 1);
+    ColRest<C, T, N, E, B, true, 1, NP>::run(v, s, l, t, tw);  // starts with a block barrier
+
+    typedef PassIdx<N, E, NP - 1> PLast;
+    __syncthreads();
+    {
+        const int u = PLast::out_u(t);
+#pragma unroll
+        for (int b = 0; b < PLast::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < PLast::R; ++r) s[S::at_k(u, l, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
+    }
+    __syncthreads();
+    const int le = Ef::line(tid);
+    const long long Le = L0 + le;
+    if (Le < a.nlines) {
+        C* dst = static_cast<C*>(a.dst) + lbase(a.out, Le);
+        if constexpr (DST) {
+            for (int c = Ef::chunk0(tid); c < M - 1; c += Ef::STEP) {
+                const C x = s[S::at(c + 1, le)];
+                dst[c] = mk<C>(-x.y, x.x);
+            }
+        } else if constexpr (DCT) {
+            for (int c = Ef::chunk0(tid); c < M + 1; c += Ef::STEP) dst[c] = s[S::at(c, le)];
+        } else {
+            typedef typename Vec4<T>::t V;
+            V* dst4 = reinterpret_cast<V*>(dst);
+            for (int c = Ef::chunk0(tid); c < N / 2; c += Ef::STEP) {
+                const C x0 = s[S::at(2 * c, le)], x1 = s[S::at(2 * c + 1, le)];
+                dst4[c] = V{x0.x, x0.y, x1.x, x1.y};
+            }
+        }
+    }
+}
+
+template <typename T, int N, int B> __host__ __device__ constexpr size_t col_tma_smem(int sym)
+{
+    typedef typename CxT<T>::t C;
+    const size_t slots = (size_t)col_smem_slots<T, N>() * B * sizeof(C);
+    const size_t tx = sym == 1 ? tma_tile_bytes<T, N, B, 1>() : sym == 2 ? tma_tile_bytes<T, N, B, 2>()
+                                                                         : tma_tile_bytes<T, N, B, 0>();
+    return (slots > tx ? slots : tx) + 128 + 16;
+}
+
+// ---------------------------------------------------------------------------
 // Persistent, software-pipelined column kernels.  Each CTA walks tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...; while it transforms tile i out of
 // one shared-memory buffer, cp.async copies of tile i + gridDim.x's

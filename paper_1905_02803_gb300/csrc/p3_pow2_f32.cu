@@ -24,6 +24,10 @@ template <int N, bool INV, int SYM> void* zrow_fn()
     else
         return nullptr;
 }
+template <int N, int SYM> void* tma_fn()
+{
+    return (void*)col_kernel_tma<float, N, col_E<float>(N, 1), col_B<float>(N), SYM>;
+}
 template <int N, int OPR> void* row_fn() { return (void*)row_kernel<float, N, row_E<float>(N), row_B<float>(N), OPR>; }
 
 // sym: 0 plain, 1 Chebyshev (DCT-I), 2 sine (DST-I, forward sign only)
@@ -62,6 +66,29 @@ void* pow2_pick_f32(int kind, int N, bool inv, int sym, bool pl)
     case 2048: return pick_n<2048>(kind, inv, sym, pl);
     case 4096: return pick_n<4096>(kind, inv, sym, pl);
     default: return nullptr;
+    }
+}
+
+// TMA-staged ZYX-store kernels (FP32, 256 .. 2048 points): kernel and dynamic shared memory
+void* pow2_pick_tma_f32(int N, int sym)
+{
+    switch (N) {
+    case 256: return sym == 2 ? tma_fn<256, 2>() : sym ? tma_fn<256, 1>() : tma_fn<256, 0>();
+    case 512: return sym == 2 ? tma_fn<512, 2>() : sym ? tma_fn<512, 1>() : tma_fn<512, 0>();
+    case 1024: return sym == 2 ? tma_fn<1024, 2>() : sym ? tma_fn<1024, 1>() : tma_fn<1024, 0>();
+    case 2048: return sym == 2 ? tma_fn<2048, 2>() : sym ? tma_fn<2048, 1>() : tma_fn<2048, 0>();
+    default: return nullptr;
+    }
+}
+size_t pow2_tma_smem_f32(int N, int sym)
+{
+    using namespace pw;
+    switch (N) {
+    case 256: return col_tma_smem<float, 256, col_B<float>(256)>(sym);
+    case 512: return col_tma_smem<float, 512, col_B<float>(512)>(sym);
+    case 1024: return col_tma_smem<float, 1024, col_B<float>(1024)>(sym);
+    case 2048: return col_tma_smem<float, 2048, col_B<float>(2048)>(sym);
+    default: return 0;
     }
 }
 

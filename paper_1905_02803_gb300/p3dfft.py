@@ -23,6 +23,7 @@ P3_FLAG_TC_SPLIT = 1
 P3_FLAG_PADDED_REAL = 2
 P3_FLAG_NO_FUSE = 4
 P3_FLAG_TUNE = 8
+P3_FLAG_NO_TMA = 16
 
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",

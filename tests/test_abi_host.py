@@ -61,7 +61,7 @@ FFT3 = (P.P3_FFT, P.P3_FFT, P.P3_FFT)
     ((8, -1, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, 7, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, FFT3, 5, 0), P.P3_ERR_INVALID),
-    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 16), P.P3_ERR_INVALID),
+    ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 32), P.P3_ERR_INVALID),
     ((8, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, P.P3_FLAG_PADDED_REAL), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 8, P.P3_F32, (P.P3_FFT, P.P3_FFT, 9), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),
     ((8, 8, 1, P.P3_F64, (P.P3_FFT, P.P3_FFT, P.P3_CHEB), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_INVALID),

@@ -1,0 +1,36 @@
+"""TMA-staged forward Z stage (ZYX store): the input tile arrives by tensor
+copies instead of per-thread loads; the arithmetic is the column kernel's, so
+the result equals the plan with P3_FLAG_NO_TMA bit for bit, and the oracle
+within the FP32 tolerance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1905_02803_gb300 import inputs
+
+from _gpu_helpers import TOL, TT, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((64, 32, 1024), ("fft", "fft", "fft")), ((32, 24, 256), ("fft", "fft", "fft")),
+         ((48, 20, 512), ("fft", "fft", "fft")), ((16, 8, 2048), ("fft", "fft", "fft")),
+         ((40, 12, 257), ("fft", "fft", "cheb")), ((36, 10, 511), ("fft", "fft", "sine")),
+         ((1024, 256, 1024), ("fft", "fft", "fft")), ((30, 7, 1025), ("fft", "empty", "cheb"))]
+
+
+@pytest.mark.parametrize("shape,tt", CASES)
+def test_tma_zyx_store_matches(shape, tt):
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = shape
+    pt = P.Plan(nx, ny, nz, precision="f32", ttypes=tt, layout="zyx")
+    pn = P.Plan(nx, ny, nz, precision="f32", ttypes=tt, layout="zyx", flags=P.P3_FLAG_NO_TMA)
+    assert "zyx_store_tma" in pt.describe() and "zyx_store_tma" not in pn.describe(), pt.describe()
+    x = torch.from_numpy(inputs.uniform_field((nz, ny, nx), nz)).to("cuda", torch.float32)
+    Xt, Xn = pt.forward(x), pn.forward(x)
+    torch.cuda.synchronize()
+    assert torch.equal(Xt, Xn)
+    assert P.p3_plan_wait_status(pt.handle) == P.P3_OK
+    if nx * ny * nz <= 1 << 22:
+        ref = O.to_zyx(O.forward(x.double().cpu().numpy(), tuple(TT[t] for t in tt)))
+        assert rel_l2(Xt.cpu().numpy(), ref) <= TOL["f32"]
