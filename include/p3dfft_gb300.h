@@ -125,9 +125,11 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                size plus a workspace for the duration of the call, so plan
  *                creation takes milliseconds to a second; the timings appear
  *                in p3_plan_describe().
- *              P3_FLAG_NO_TMA: load the forward ZYX-store Z stage's input
- *                tiles with ordinary loads instead of tensor-memory-access
- *                (TMA) copies (FP32 Z lines of 256 .. 2048 points).
+ *              P3_FLAG_NO_TMA: load the Z stages' input tiles with ordinary
+ *                loads instead of tensor-memory-access (TMA) copies: the
+ *                forward ZYX-store stage (FP32 lines of 256 .. 2048 points)
+ *                and the inverse ZYX-load stage when its lines lie one after
+ *                another in memory (FP32 FFT lines of 256 .. 1024 points).
  * Any line length is accepted: lengths whose prime factors are 2, 3, 5, 7 run
  * natively; other lengths use Bluestein's chirp-z algorithm.  Lines longer
  * than 4096 points (2048 when Bluestein is needed) return P3_ERR_UNSUPPORTED.

@@ -94,7 +94,8 @@ struct StageArgs {
     int persist;
     // 1: tensor-core split-precision kernel (p3_tc.cu)
     int tc;
-    // 1: TMA-staged ZYX-store column kernel (input tile by tensor copies)
+    // 1: TMA-staged ZYX-store column kernel (input tile by tensor copies);
+    // 2: row-style ZYX-load kernel with a bulk-copied input tile
     int tma;
     // status word of the plan: a bounded device wait that gave up ORs a bit in
     unsigned* err;

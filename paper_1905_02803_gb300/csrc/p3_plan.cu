@@ -315,6 +315,7 @@ const char* op_name(int op)
 const char* kern_name(int k, int tc, int tma = 0)
 {
     if (tc) return "tc_split_col";
+    if (tma == 2) return "pow2_zrow_bulk";
     if (tma) return "pow2_col_zyx_store_tma";
     switch (k) {
     case p3::KIND_COL_DD: return "pow2_col";
@@ -683,6 +684,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
                 z.a.in = zyx_lines;
                 z.a.out = ws_lines;
             }
+            // same kernel kind; the new maps can admit a TMA-fed variant
+            if (z.a.kern != p3::KIND_GENERIC) p3::pow2_configure(z.a, P->csize, !(flags & P3_FLAG_NO_TMA));
         }
     }
     const bool any_fused = fuse_at[0] >= 0 || fuse_at[1] >= 0 || fuse_at[2] >= 0;
@@ -963,7 +966,7 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
             f.extra = P->wait_extra;
             e = p3::fused_launch(f, s);
         } else {
-            e = a.tma ? p3::pow2_encode_tma(a) : cudaSuccess;
+            e = a.tma == 1 ? p3::pow2_encode_tma(a) : cudaSuccess;
             if (e == cudaSuccess) e = P->prec == P3_F32 ? p3::launch_stage_f32(a, s) : p3::launch_stage_f64(a, s);
         }
         if (e != cudaSuccess) return P3_ERR_CUDA;

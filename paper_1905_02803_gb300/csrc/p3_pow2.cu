@@ -14,6 +14,8 @@ void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* sm
 
 void* pow2_pick_tma_f32(int N, int sym);
 size_t pow2_tma_smem_f32(int N, int sym);
+void* pow2_pick_zbulk_f32(int N);
+size_t pow2_zbulk_smem_f32(int N);
 
 // Column-kernel symmetry variant of a stage: 0 plain, 1 DCT-I, 2 DST-I.
 static int sym_of(const StageArgs& a) { return a.op == OP_DCT1 ? 1 : a.op == OP_DST1 ? 2 : 0; }
@@ -73,6 +75,13 @@ static bool configure(StageArgs& a, size_t csize, bool allow_tma)
         a.tma = 1;
         a.smem = pow2_tma_smem_f32(N, sym_of(a));
     }
+    // bulk-copied tile for the row-style ZYX load: plain FFT lines that lie
+    // one after another in memory
+    if (f32 && allow_tma && kind == KIND_COL_SD && !pl && a.op == OP_C2C && a.sign > 0 && a.n_in == N &&
+        a.in.es == 1 && a.in.lstride == N && a.in.per >= a.nlines && a.gcount == 0 && pow2_pick_zbulk_f32(N)) {
+        a.tma = 2;
+        a.smem = pow2_zbulk_smem_f32(N);
+    }
     if (pl) {
         // persistent grid: resident CTAs per SM times the SM count
         void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, sym_of(a), true)
@@ -100,6 +109,12 @@ cudaError_t pow2_prepare()
                     for (int sym = 0; sym < 3; ++sym)
                         for (int pl = 0; pl < 2; ++pl) {
                             void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, sym, pl) : pow2_pick_f64(kind, N, inv, sym, pl);
+                            if (f == 0 && kind == KIND_COL_SD && inv && !pl && sym == 0) {
+                                void* fb = pow2_pick_zbulk_f32(N);
+                                if (fb && cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               227 * 1024) != cudaSuccess)
+                                    return cudaGetLastError();
+                            }
                             if (f == 0 && kind == KIND_COL_DS && !inv && !pl) {
                                 void* ft = pow2_pick_tma_f32(N, sym);
                                 if (ft && cudaFuncSetAttribute(ft, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -118,7 +133,8 @@ cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
 {
     const bool inv = a.sign > 0, pl = a.persist > 0;
     const int sym = sym_of(a);
-    void* fn = a.tma ? pow2_pick_tma_f32(a.nfft, sym)
+    void* fn = a.tma == 2 ? pow2_pick_zbulk_f32(a.nfft)
+               : a.tma ? pow2_pick_tma_f32(a.nfft, sym)
                      : (f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym, pl) : pow2_pick_f64(a.kern, a.nfft, inv, sym, pl));
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;

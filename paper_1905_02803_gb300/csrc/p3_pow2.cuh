@@ -816,11 +816,22 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 // tile's B adjacent lines (B-wide runs of the XYZ output).  Input lines must
 // have unit element stride.  SYM as in col_tile.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int E, int B, bool INV, int SYM>
+template <typename T, int N, int E, int B> __host__ __device__ constexpr size_t zrow_area()
+{
+    typedef typename CxT<T>::t C;
+    const size_t ex = (size_t)B * (size_t)RowSlot<N, E>::RP, res = (size_t)N * (size_t)B;
+    return (ex > res ? ex : res) * sizeof(C);
+}
+
+// BULK: the tile's B lines are consecutive in memory (plain FFT lines), so
+// one bulk copy brings them into shared memory against an mbarrier (bounded
+// wait, as in col_kernel_tma) and the first pass reads them from there.
+template <typename T, int N, int E, int B, bool INV, int SYM, bool BULK = false>
 __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeof(T), E>::value))
     zrow_kernel(const __grid_constant__ StageArgs a)
 {
     static_assert(SYM != 2 || !INV, "the sine transform always runs with the forward sign");
+    static_assert(!BULK || SYM == 0, "bulk tiles of whole, even-length lines");
     constexpr bool DCT = SYM == 1, DST = SYM == 2;
     typedef typename CxT<T>::t C;
     typedef P2<N, E> PL;
@@ -833,7 +844,8 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     static_assert(NT % B == 0 && B >= 4, "store lanes keep their line");
     typedef RowSlot<N, E> S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
+    unsigned char* base = BULK ? smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u) : smem_raw;
+    C* s = reinterpret_cast<C*>(base);
     const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
     const long long L0 = (long long)blockIdx.x * B;
     const long long L = L0 + l;
@@ -843,7 +855,43 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     C v[E];
     typedef PassIdx<N, E, 0> P0;
     typedef PassIdx<N, E, NP - 1> PLast;
-    {
+    if constexpr (BULK) {
+        const unsigned bar = smem_u32(base + zrow_area<T, N, E, B>());
+        const long long left = a.nlines - L0;
+        const unsigned bytes = (unsigned)((left < B ? left : B) * N * (long long)sizeof(C));
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                             smem_u32(s)),
+                         "l"(static_cast<const C*>(a.src) + lbase(a.in, L0)), "r"(bytes), "r"(bar)
+                         : "memory");
+        }
+        int ok = 0;
+        for (unsigned it = 0; it < kTmaSpin; ++it)
+            if (mbar_try_wait(bar, 0)) {
+                ok = 1;
+                break;
+            }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(a.err, 2u);
+            for (unsigned it = 0; it < kTmaSpin && !mbar_try_wait(bar, 0); ++it) {
+            }
+            return;
+        }
+#pragma unroll
+        for (int b = 0; b < P0::BM; ++b)
+#pragma unroll
+            for (int r = 0; r < P0::R; ++r) {
+                const C x = valid ? s[l * N + t + P0::in_K(b, r)] : zero;
+                v[b * P0::R + r] = INV ? swp(x) : x;
+            }
+        __syncthreads();  // the exchange rows overlap the bulk tile
+    } else {
         const C* src = static_cast<const C*>(a.src) + (valid ? lbase(a.in, L) : 0);
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
@@ -892,9 +940,11 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
 
 template <typename T, int N, int E, int B> __host__ __device__ constexpr size_t zrow_smem()
 {
-    typedef typename CxT<T>::t C;
-    const size_t ex = (size_t)B * (size_t)RowSlot<N, E>::RP, res = (size_t)N * (size_t)B;
-    return (ex > res ? ex : res) * sizeof(C);
+    return zrow_area<T, N, E, B>();
+}
+template <typename T, int N, int E, int B> __host__ __device__ constexpr size_t zrow_bulk_smem()
+{
+    return zrow_area<T, N, E, B>() + 128 + 16;
 }
 
 // ---------------------------------------------------------------------------

@@ -69,6 +69,27 @@ void* pow2_pick_f32(int kind, int N, bool inv, int sym, bool pl)
     }
 }
 
+// Row-style ZYX-load kernels with a bulk-copied input tile (FP32 plain FFT lines, 256 .. 1024 points)
+void* pow2_pick_zbulk_f32(int N)
+{
+    switch (N) {
+    case 256: return (void*)zrow_kernel<float, 256, row_E<float>(256), row_B<float>(256), true, 0, true>;
+    case 512: return (void*)zrow_kernel<float, 512, row_E<float>(512), row_B<float>(512), true, 0, true>;
+    case 1024: return (void*)zrow_kernel<float, 1024, row_E<float>(1024), row_B<float>(1024), true, 0, true>;
+    default: return nullptr;
+    }
+}
+size_t pow2_zbulk_smem_f32(int N)
+{
+    using namespace pw;
+    switch (N) {
+    case 256: return zrow_bulk_smem<float, 256, row_E<float>(256), row_B<float>(256)>();
+    case 512: return zrow_bulk_smem<float, 512, row_E<float>(512), row_B<float>(512)>();
+    case 1024: return zrow_bulk_smem<float, 1024, row_E<float>(1024), row_B<float>(1024)>();
+    default: return 0;
+    }
+}
+
 // TMA-staged ZYX-store kernels (FP32, 256 .. 2048 points): kernel and dynamic shared memory
 void* pow2_pick_tma_f32(int N, int sym)
 {

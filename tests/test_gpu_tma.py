@@ -34,3 +34,25 @@ def test_tma_zyx_store_matches(shape, tt):
     if nx * ny * nz <= 1 << 22:
         ref = O.to_zyx(O.forward(x.double().cpu().numpy(), tuple(TT[t] for t in tt)))
         assert rel_l2(Xt.cpu().numpy(), ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024, 64), (512, 256, 1024), (512, 512, 256), (1024, 256, 512)])
+def test_bulk_zyx_load_matches(shape):
+    """Inverse Z stage of a plane-fused ZYX plan (transposed planes): its
+    input lines lie one after another, so the row-style kernel takes the
+    tile with one bulk copy; bit-identical to P3_FLAG_NO_TMA."""
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = shape
+    pt = P.Plan(nx, ny, nz, precision="f32", layout="zyx")
+    pn = P.Plan(nx, ny, nz, precision="f32", layout="zyx", flags=P.P3_FLAG_NO_TMA)
+    d = pt.describe()
+    if nz >= 256:
+        assert "pow2_zrow_bulk" in d, d
+    assert "pow2_zrow_bulk" not in pn.describe()
+    G = torch.from_numpy(np.asarray(inputs.normal(5, 1, 2 * (nx // 2 + 1) * ny * nz), dtype=np.float32)).cuda()
+    X = torch.view_as_complex(G.view(nx // 2 + 1, ny, nz, 2))
+    yt, yn = pt.backward(X), pn.backward(X)
+    torch.cuda.synchronize()
+    assert torch.equal(yt, yn)
+    assert P.p3_plan_wait_status(pt.handle) == P.P3_OK
