@@ -69,7 +69,7 @@ __device__ __forceinline__ void xr2c_tile_t(const StageArgs& a, long long L0, ty
             for (int r = 0; r < P0::R; ++r) v[b * P0::R + r] = ldx<LP>(src + t + P0::in_K(b, r));
     }
     pass_compute<C, T, N, E, 0>(v, t, tw2, 2);
-    RowRest<C, T, N, E, 1, NP>::run(v, srow, t, tw2);
+    RowRest<C, T, N, E, 1, NP, 0>::run(v, srow, t, static_cast<const C*>(a.twr));
     row_sync<TPL>();
     {
         const int u = PLast::out_u(t);
@@ -145,7 +145,7 @@ __device__ __forceinline__ void xc2r_tile_t(const StageArgs& a, long long L0, co
         }
     __syncthreads();  // the exchange rows overlap the transposed tile
     pass_compute<C, T, N, E, 0>(v, t, tw2, 2);
-    RowRest<C, T, N, E, 1, NP>::run(v, s + l * S::RP, t, tw2);
+    RowRest<C, T, N, E, 1, NP, 0>::run(v, s + l * S::RP, t, static_cast<const C*>(a.twr));
     C* dst = reinterpret_cast<C*>(static_cast<T*>(a.dst) + L * a.out.lstride);
     const int u = PLast::out_u(t);
 #pragma unroll
@@ -181,7 +181,7 @@ __device__ __forceinline__ void line_tile(const StageArgs& a, typename CxT<T>::t
             v[b * P0::R + r] = INV ? swp(x) : x;
         }
     pass_compute<C, T, N, E, 0>(v, t, tw, 1);
-    RowRest<C, T, N, E, 1, NP, 1>::run(v, s + l * S::RP, t, tw);
+    RowRest<C, T, N, E, 1, NP, 0>::run(v, s + l * S::RP, t, static_cast<const C*>(a.twr));
     if (valid) {
         const int u = PLast::out_u(t);
 #pragma unroll

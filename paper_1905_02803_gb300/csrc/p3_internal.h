@@ -72,6 +72,7 @@ struct StageArgs {
     const void* tw;    // tw[k] = exp(-2 pi i k / twn), complex of the stage type
     int twn;
     const void* tw2;   // real-split twiddles exp(-2 pi i k / Nx) (R2C/C2R_HALF), length Nx
+    const void* twr;   // power-of-two lines: per-pass twiddles laid out for row-style lanes
     // Bluestein (nfft not 7-smooth): DFT_nfft via padded length m
     int blue;
     int m;

@@ -206,6 +206,33 @@ size_t roots_table(TableSet& T, long long n)
     return T.add(TableKey{0, n, 0}, std::move(v));
 }
 
+// Per-pass twiddles of a power-of-two line of n points with E values per
+// thread, laid out for row-style lanes (see rtw_off in p3_pow2.cuh): pass
+// p >= 1 (NS = the product of the earlier radices, radix R, step n/(NS R))
+// stores, at (r - 1) NS + q, the entry the roots table of length tn gives at
+// index q step r (tn / n).
+size_t row_tw_table(TableSet& T, long long n, int E, long long tn)
+{
+    int logn = 0, loge = 0;
+    while ((1LL << logn) < n) ++logn;
+    while ((1 << loge) < E) ++loge;
+    const int nfull = logn / loge;
+    const long long rem = 1LL << (logn - nfull * loge);
+    const int npass = nfull + (rem > 1 ? 1 : 0);
+    std::vector<std::complex<double>> v;
+    long long ns = 1;
+    for (int p = 0; p < npass; ++p) {
+        const long long R = p < nfull ? E : rem;
+        if (p >= 1) {
+            const long long step = n / (ns * R);
+            for (long long r = 1; r < R; ++r)
+                for (long long q = 0; q < ns; ++q) v.push_back(unit_root(q * step * r * (tn / n), tn));
+        }
+        ns *= R;
+    }
+    return T.add(TableKey{3, n * 64 + E, tn}, std::move(v));
+}
+
 size_t chirp_table(TableSet& T, long long n)
 {
     std::vector<std::complex<double>> v((size_t)n);
@@ -232,7 +259,7 @@ size_t bhat_table(TableSet& T, long long n, long long m)
 // Pointer-valued table fields hold byte offsets (+1, 0 = none) until the
 // device block exists.
 struct Pending {
-    size_t tw = 0, tw2 = 0, chirp = 0, bhat = 0, twm = 0;
+    size_t tw = 0, tw2 = 0, chirp = 0, bhat = 0, twm = 0, twr = 0;
 };
 
 // Line-FFT set-up: native radices over nfft, else Bluestein over m.
@@ -541,6 +568,13 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         if (a.op != p3::OP_COPY) {
             rc = line_setup(a, pd, T, twn);
             if (rc != P3_OK) return;
+            // row-style twiddles for power-of-two lines (E as the row kernels take it)
+            const long long n = a.nfft;
+            if (!a.blue && n >= 64 && n <= 4096 && (n & (n - 1)) == 0) {
+                const int E = (prec == P3_F32 && n >= 512 && n <= 2048) ? 32 : 16;
+                const bool half = a.op == p3::OP_R2C_HALF || a.op == p3::OP_C2R_HALF;
+                pd.twr = row_tw_table(T, n, E, half ? 2 * n : n) + 1;
+            }
         } else {
             a.tpl = 1;
             a.nfft = a.n_in;  // slots per line; no FFT passes
@@ -747,7 +781,9 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.chirp = resolve(pd.chirp);
             a.bhat = resolve(pd.bhat);
             a.twm = resolve(pd.twm);
+            a.twr = resolve(pd.twr);
             StageArgs& b = unfused[d][i].a;
+            b.twr = a.twr;
             b.tw = a.tw;
             b.tw2 = a.tw2;
             b.chirp = a.chirp;

@@ -154,6 +154,31 @@ __device__ __forceinline__ void pass_compute(C (&v)[E], int t, const C* tw, int 
     }
 }
 
+// Row-twiddle tables: for lanes that run along a line (row-style kernels),
+// the twiddles of pass P >= 1 are stored as entry (r - 1) NS + q, q = j % NS,
+// so the lanes of a warp (consecutive j) read consecutive entries instead of
+// entries j r apart.  Passes follow one another in one table.
+template <int N, int E> __host__ __device__ constexpr int rtw_off(int P)
+{
+    return P <= 1 ? 0 : rtw_off<N, E>(P - 1) + (P2<N, E>::radix(P - 1) - 1) * P2<N, E>::ns(P - 1);
+}
+
+template <class C, class T, int N, int E, int P>
+__device__ __forceinline__ void pass_compute_r(C (&v)[E], int t, const C* twr)
+{
+    typedef PassIdx<N, E, P> PI;
+    constexpr int R = PI::R, NS = PI::NS, OFF = rtw_off<N, E>(P);
+#pragma unroll
+    for (int b = 0; b < PI::BM; ++b) {
+        if constexpr (NS > 1) {
+            const int q = (t + b * PI::TPL) % NS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b * R + r] = mul(v[b * R + r], ldg(twr + OFF + (r - 1) * NS + q));
+        }
+        Dft<C, T, R>::run(&v[b * R]);
+    }
+}
+
 // Exchanges and passes 1 .. NP-1 through a column tile in shared memory.
 template <class C, class T, int N, int E, int B, bool SWZ, int P, int NP> struct ColRest {
     static __device__ __forceinline__ void run(C (&v)[E], C* s, int l, int t, const C* tw)
@@ -709,7 +734,8 @@ template <class C, class T, int N, int E, int P, int NP, int TS = 2> struct RowR
         for (int b = 0; b < Cu::BM; ++b)
 #pragma unroll
             for (int r = 0; r < Cu::R; ++r) v[b * Cu::R + r] = s[S::at_k(t, Cu::in_K(b, r), 1)];
-        pass_compute<C, T, N, E, P>(v, t, tw, TS);
+        if constexpr (TS == 0) pass_compute_r<C, T, N, E, P>(v, t, tw);  // tw: row-twiddle table
+        else pass_compute<C, T, N, E, P>(v, t, tw, TS);
         RowRest<C, T, N, E, P + 1, NP, TS>::run(v, s, t, tw);
     }
 };
@@ -764,7 +790,7 @@ __device__ __forceinline__ void row_tile(const StageArgs& a, long long L0, long 
             }
     }
     pass_compute<C, T, N, E, 0>(v, t, tw2, 2);
-    RowRest<C, T, N, E, 1, NP>::run(v, srow, t, tw2);
+    RowRest<C, T, N, E, 1, NP, 0>::run(v, srow, t, static_cast<const C*>(a.twr));
 
     if constexpr (OPR == 0) {
         row_sync<N / E>();
@@ -909,7 +935,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
             }
     }
     pass_compute<C, T, N, E, 0>(v, t, tw, 1);
-    RowRest<C, T, N, E, 1, NP, 1>::run(v, s + l * S::RP, t, tw);
+    RowRest<C, T, N, E, 1, NP, 0>::run(v, s + l * S::RP, t, static_cast<const C*>(a.twr));
     __syncthreads();  // the result tile overlaps other lines' exchange rows
     {
         const int u = PLast::out_u(t);
