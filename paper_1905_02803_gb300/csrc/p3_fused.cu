@@ -226,11 +226,21 @@ __host__ __device__ constexpr size_t fused_smem()
 #ifndef P3_FUSED_NT_TP
 #define P3_FUSED_NT_TP 128
 #endif
+// Resident CTAs per SM the transposed-plane kernels are compiled for: five
+// forward (96 registers, measured 2.68 -> 2.61 ms at 1024^3), four inverse
+// (its c2r tile spills at 96)
+#ifndef P3_FUSED_MINB_TP_FWD
+#define P3_FUSED_MINB_TP_FWD 5
+#endif
+#ifndef P3_FUSED_MINB_TP_INV
+#define P3_FUSED_MINB_TP_INV 4
+#endif
 
 // NX: half length of the real X rows (complex points), NY: Y line length,
 // NT: threads per CTA (both tile kinds), TP: transposed planes.
 template <typename T, int NX, int NY, int DIR, int NT, bool TP>
-__global__ void __launch_bounds__(NT, 512 / NT) plane_kernel(const __grid_constant__ PlaneArgs f)
+__global__ void __launch_bounds__(NT, (TP ? (DIR == 0 ? P3_FUSED_MINB_TP_FWD : P3_FUSED_MINB_TP_INV) : 512 / NT))
+    plane_kernel(const __grid_constant__ PlaneArgs f)
 {
     typedef typename CxT<T>::t C;
     constexpr int EX = fx_E<T>(NX), BX = fx_B<T>(NX, NT);
