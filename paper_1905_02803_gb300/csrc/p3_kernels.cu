@@ -239,22 +239,45 @@ __global__ void __launch_bounds__(kMaxThreads, 2) stage_kernel(const __grid_cons
     C* s1 = s0 + (size_t)nload * LDB;  // second buffer of the ping-pong passes
 
     // ---- load: HBM -> shared memory ------------------------------------
+    // KB loads of a thread are issued before any of them is stored, so
+    // their latencies overlap instead of adding up
+    constexpr int KB = sizeof(T) == 4 ? 8 : 4;
+    const C zero = mk<C>((T)0, (T)0);
     if (a.in_elem_fast) {
         const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
         for (int l = warp; l < B; l += nw) {
             const long long L = L0 + l;
             if (L >= a.nlines) break;
             const long long base = line_base(a.in, L);
-            for (int e = lane; e < nload; e += 32)
-                s0[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
+            for (int e0 = lane; e0 < nload; e0 += 32 * KB) {
+                C w[KB];
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    const int e = e0 + 32 * k;
+                    w[k] = e < nfill ? load_value<C, T>(a, base, e) : zero;
+                }
+#pragma unroll
+                for (int k = 0; k < KB; ++k)
+                    if (e0 + 32 * k < nload) s0[(e0 + 32 * k) * LDB + l] = w[k];
+            }
         }
     } else {
         const int l = tid & (B - 1);
         const long long L = L0 + l;
         if (L < a.nlines) {
             const long long base = line_base(a.in, L);
-            for (int e = tid / B; e < nload; e += NT / B)
-                s0[e * LDB + l] = e < nfill ? load_value<C, T>(a, base, e) : mk<C>((T)0, (T)0);
+            const int st = NT / B;
+            for (int e0 = tid / B; e0 < nload; e0 += st * KB) {
+                C w[KB];
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    const int e = e0 + st * k;
+                    w[k] = e < nfill ? load_value<C, T>(a, base, e) : zero;
+                }
+#pragma unroll
+                for (int k = 0; k < KB; ++k)
+                    if (e0 + st * k < nload) s0[(e0 + st * k) * LDB + l] = w[k];
+            }
         }
     }
     __syncthreads();
