@@ -39,11 +39,11 @@ template <int B> __device__ __forceinline__ int tsw(int k) { return (k >> (B >= 
 // stage's input), written to plane[k * ny + y0 + l].  The rows' last-pass
 // outputs go to shared memory once; the store lanes (across rows) read
 // Z[k] and Z[N-k] there and write the post-twiddled F[k] straight to the
-// plane.  Row pitch RPX = 4 (mod 16) complex keeps those cross-row reads on
-// distinct banks.
-template <int N, int E> __host__ __device__ constexpr int xt_pitch()
+// plane.  Row pitch RPX = 16/B (mod 16) complex keeps those cross-row reads
+// on distinct banks (a half-warp covers the B rows at 16/B consecutive k).
+template <int N, int E, int B> __host__ __device__ constexpr int xt_pitch()
 {
-    return (N + N / E) + ((4 - (N + N / E) % 16) + 16) % 16;
+    return (N + N / E) + ((16 / B - (N + N / E) % 16) % 16 + 16) % 16;
 }
 
 template <typename T, int N, int E, int B, int LP>
@@ -52,7 +52,7 @@ __device__ __forceinline__ void xr2c_tile_t(const StageArgs& a, long long L0, ty
 {
     typedef typename CxT<T>::t C;
     typedef P2<N, E> PL;
-    constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL, RPX = xt_pitch<N, E>();
+    constexpr int TPL = PL::TPL, NP = PL::NPASS, NT = B * TPL, RPX = xt_pitch<N, E, B>();
     typedef RowSlot<N, E> S;
     const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
     const long long L = L0 + l;
@@ -211,8 +211,8 @@ __host__ __device__ constexpr size_t fused_smem()
     const size_t bx = (size_t)fx_B<T>(NX, NT);
     size_t row = bx * (size_t)(NX + NX / fx_E<T>(NX) + 1) * sizeof(C);
     if (TP && bx * (size_t)(NX + 1) * sizeof(C) > row) row = bx * (size_t)(NX + 1) * sizeof(C);
-    if (TP && bx * (size_t)xt_pitch<NX, fx_E<T>(NX)>() * sizeof(C) > row)
-        row = bx * (size_t)xt_pitch<NX, fx_E<T>(NX)>() * sizeof(C);
+    if (TP && bx * (size_t)xt_pitch<NX, fx_E<T>(NX), fx_B<T>(NX, NT)>() * sizeof(C) > row)
+        row = bx * (size_t)xt_pitch<NX, fx_E<T>(NX), fx_B<T>(NX, NT)>() * sizeof(C);
     const size_t col = TP ? (size_t)fl_B<T>(NY, NT) * (size_t)(NY + NY / fl_E<T>(NY) + 1) * sizeof(C)
                           : (size_t)fy_B<T>(NY, NT) * (size_t)col_smem_slots<T, NY>() * sizeof(C);
     return row > col ? row : col;
