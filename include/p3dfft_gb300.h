@@ -112,7 +112,8 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                works in its output buffer and leaves the input untouched.
  *              P3_FLAG_NO_FUSE: launch the X and Y stages separately.  By
  *                default, where a fused kernel exists (FP32, even Nx with
- *                Nx/2 and Ny in {256, 512, 1024}, FFT in Y, no padded rows,
+ *                Nx/2 in {256, 512, 1024} and Ny in {256, 512, 1024, 2048},
+ *                FFT in Y, no padded rows,
  *                no tensor-core split), the X and Y stages of each direction
  *                run as one persistent launch that works z-plane by z-plane
  *                so the second stage reads the first one's output from L2.

@@ -362,6 +362,7 @@ template <int NX> void* pick_ny(int ny, int dir, bool tp)
     case 256: return pick_dir<NX, 256>(dir, tp);
     case 512: return pick_dir<NX, 512>(dir, tp);
     case 1024: return pick_dir<NX, 1024>(dir, tp);
+    case 2048: return pick_dir<NX, 2048>(dir, tp);
     default: return nullptr;
     }
 }
@@ -382,6 +383,7 @@ template <int NT, bool TP> size_t smem_nt(int nx, int ny)
     P3_SM(256, 256) P3_SM(256, 512) P3_SM(256, 1024)
     P3_SM(512, 256) P3_SM(512, 512) P3_SM(512, 1024)
     P3_SM(1024, 256) P3_SM(1024, 512) P3_SM(1024, 1024)
+    P3_SM(256, 2048) P3_SM(512, 2048) P3_SM(1024, 2048)
 #undef P3_SM
     return m;
 }

@@ -1013,7 +1013,7 @@ template <typename T> __host__ __device__ constexpr int col_pl_E(int N, int mode
 #endif
 template <typename T> __host__ __device__ constexpr bool col_zrow(int N)
 {
-    return P3_ZROW && sizeof(T) == 4 && N >= 256 && N <= 1024;
+    return P3_ZROW && sizeof(T) == 4 && N >= 256 && N <= 2048;
 }
 #ifndef P3_ROW_E32
 #define P3_ROW_E32 1
@@ -1028,6 +1028,9 @@ template <typename T> __host__ __device__ constexpr int row_B(int N)
 {
     return (256 / (N / row_E<T>(N))) > 0 ? 256 / (N / row_E<T>(N)) : 1;
 }
+// lines per tile of the row-style ZYX-load kernel: a CTA of 256 threads, or
+// 8 lines (512 threads) at 2048 points so the strided stores keep 64-byte runs
+template <typename T> __host__ __device__ constexpr int zrow_B(int N) { return N >= 2048 ? 8 : row_B<T>(N); }
 
 }  // namespace pw
 }  // namespace p3

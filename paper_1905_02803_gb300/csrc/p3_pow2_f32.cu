@@ -20,7 +20,7 @@ template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
 template <int N, bool INV, int SYM> void* zrow_fn()
 {
     if constexpr (col_zrow<float>(N))
-        return (void*)zrow_kernel<float, N, row_E<float>(N), row_B<float>(N), INV, SYM>;
+        return (void*)zrow_kernel<float, N, row_E<float>(N), zrow_B<float>(N), INV, SYM>;
     else
         return nullptr;
 }
@@ -76,6 +76,7 @@ void* pow2_pick_zbulk_f32(int N)
     case 256: return (void*)zrow_kernel<float, 256, row_E<float>(256), row_B<float>(256), true, 0, true>;
     case 512: return (void*)zrow_kernel<float, 512, row_E<float>(512), row_B<float>(512), true, 0, true>;
     case 1024: return (void*)zrow_kernel<float, 1024, row_E<float>(1024), row_B<float>(1024), true, 0, true>;
+    case 2048: return (void*)zrow_kernel<float, 2048, row_E<float>(2048), zrow_B<float>(2048), true, 0, true>;
     default: return nullptr;
     }
 }
@@ -86,6 +87,7 @@ size_t pow2_zbulk_smem_f32(int N)
     case 256: return zrow_bulk_smem<float, 256, row_E<float>(256), row_B<float>(256)>();
     case 512: return zrow_bulk_smem<float, 512, row_E<float>(512), row_B<float>(512)>();
     case 1024: return zrow_bulk_smem<float, 1024, row_E<float>(1024), row_B<float>(1024)>();
+    case 2048: return zrow_bulk_smem<float, 2048, row_E<float>(2048), zrow_B<float>(2048)>();
     default: return 0;
     }
 }
@@ -124,12 +126,13 @@ void pow2_shape_f32(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* sm
         *smem = (size_t)(*B) * (size_t)(N + N / E + 1) * sizeof(float) * 2;
     } else if (kind == KIND_COL_SD && col_zrow<float>(N)) {
         const int E = row_E<float>(N);
-        *B = row_B<float>(N);
+        *B = zrow_B<float>(N);
         *tpl = N / E;
         switch (N) {
-        case 256: *smem = zrow_smem<float, 256, row_E<float>(256), row_B<float>(256)>(); break;
-        case 512: *smem = zrow_smem<float, 512, row_E<float>(512), row_B<float>(512)>(); break;
-        default: *smem = zrow_smem<float, 1024, row_E<float>(1024), row_B<float>(1024)>(); break;
+        case 256: *smem = zrow_smem<float, 256, row_E<float>(256), zrow_B<float>(256)>(); break;
+        case 512: *smem = zrow_smem<float, 512, row_E<float>(512), zrow_B<float>(512)>(); break;
+        case 1024: *smem = zrow_smem<float, 1024, row_E<float>(1024), zrow_B<float>(1024)>(); break;
+        default: *smem = zrow_smem<float, 2048, row_E<float>(2048), zrow_B<float>(2048)>(); break;
         }
     } else {
         const int mode = kind == KIND_COL_SD ? 2 : kind == KIND_COL_DS ? 1 : 0;

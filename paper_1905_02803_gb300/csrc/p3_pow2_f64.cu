@@ -20,7 +20,7 @@ template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
 template <int N, bool INV, int SYM> void* zrow_fn()
 {
     if constexpr (col_zrow<double>(N))
-        return (void*)zrow_kernel<double, N, row_E<double>(N), row_B<double>(N), INV, SYM>;
+        return (void*)zrow_kernel<double, N, row_E<double>(N), zrow_B<double>(N), INV, SYM>;
     else
         return nullptr;
 }
