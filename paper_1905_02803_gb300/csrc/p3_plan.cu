@@ -810,14 +810,15 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         f.yt = (int)((H + f.by - 1) / f.by);
         // lag: about three (forward) or one and a half (inverse) grid-fulls
         // of tickets between a plane's last producer and its first consumer
-        // (measured best at 1024^3), with the planes in flight (lag + 1 of
-        // them) within 96 MB of the 129 MB L2
+        // (measured best at 1024^3), capped at the number of planes that fit
+        // in 48 MB of the 129 MB L2 (2048^3: lag 2, measured within 4 % of the
+        // best lag)
         {
             const long long per = f.xt + f.yt;
             const long long span = d == 0 ? 3LL * f.grid : 3LL * f.grid / 2;
             long long lag = (span + per - 1) / per + 1;
             const long long plane_bytes = (long long)P->csize * NY * H;
-            const long long cap = (96LL << 20) / (plane_bytes > 0 ? plane_bytes : 1) - 1;
+            const long long cap = (48LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
             if (lag > cap) lag = cap;
             if (lag > nz) lag = nz;
             if (lag < 1) lag = 1;
