@@ -14,7 +14,8 @@ from _gpu_helpers import TOL, check_case, random_complex
 
 pytestmark = pytest.mark.gpu
 
-FUSED = [(512, 256, 16), (1024, 1024, 4), (2048, 512, 6), (512, 1024, 9), (1024, 256, 1), (2048, 1024, 3)]
+FUSED = [(512, 256, 16), (1024, 1024, 4), (2048, 512, 6), (512, 1024, 9), (1024, 256, 1), (2048, 1024, 3),
+         (512, 2048, 3), (2048, 2048, 2)]
 
 
 @pytest.mark.parametrize("shape", FUSED)

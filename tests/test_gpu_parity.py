@@ -188,3 +188,13 @@ def test_sine_mode_delta_on_gpu():
     expect = np.zeros_like(X)
     expect[m - 1, 0, 0] = nx * ny * (nz + 1)
     assert np.abs(X - expect).max() < 1e-9 * nx * ny * (nz + 1)
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 2048), (24, 6, 1024), (40, 4, 512)])
+def test_row_style_zyx_load_lengths(shape):
+    """ZYX-load (inverse Z) stage of the row-style kernel at 512 .. 2048
+    points (2048: 8-line tiles of 512 threads), forward and inverse."""
+    nx, ny, nz = shape
+    ef, eb, plan = check_case(nx, ny, nz, "f32", layout="zyx", seed=nz)
+    assert "pow2_col_zyx_load" in plan.describe() or "pow2_zrow_bulk" in plan.describe()
+    assert ef <= TOL["f32"] and eb <= TOL["f32"], (ef, eb)
