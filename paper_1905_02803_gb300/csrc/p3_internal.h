@@ -91,8 +91,6 @@ struct StageArgs {
     // i * B + l.
     long long gcount;
     int glen;
-    // > 0: persistent pipelined kernel, launched with at most this many CTAs
-    int persist;
     // 1: tensor-core split-precision kernel (p3_tc.cu)
     int tc;
     // 1: TMA-staged ZYX-store column kernel (input tile by tensor copies);

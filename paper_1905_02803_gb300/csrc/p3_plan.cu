@@ -888,7 +888,6 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
                 }
                 if (n > 1) rs += std::to_string(n) + "x";
                 rs.pop_back();
-                if (a.persist > 0) rs += " persistent_ctas=" + std::to_string(a.persist);
             } else {
                 const int np = a.blue ? a.mpass : a.npass;
                 for (int i = 0; i < np; ++i) {

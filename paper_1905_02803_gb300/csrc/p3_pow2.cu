@@ -7,10 +7,10 @@
 
 namespace p3 {
 
-void* pow2_pick_f32(int kind, int N, bool inv, int sym, bool pl);
-void* pow2_pick_f64(int kind, int N, bool inv, int sym, bool pl);
-void pow2_shape_f32(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
-void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl);
+void* pow2_pick_f32(int kind, int N, bool inv, int sym);
+void* pow2_pick_f64(int kind, int N, bool inv, int sym);
+void pow2_shape_f32(int kind, int N, int* B, int* tpl, size_t* smem);
+void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem);
 
 void* pow2_pick_tma_f32(int N, int sym);
 size_t pow2_tma_smem_f32(int N, int sym);
@@ -54,48 +54,31 @@ static bool configure(StageArgs& a, size_t csize, bool allow_tma)
     } else {
         return false;
     }
-    int B = 1, tpl = 1, pl = 0;
+    int B = 1, tpl = 1;
     size_t smem = 0;
-    const bool allow_pl = a.op != OP_DST1;
-    if (f32) pow2_shape_f32(kind, N, allow_pl, &B, &tpl, &smem, &pl);
-    else pow2_shape_f64(kind, N, allow_pl, &B, &tpl, &smem, &pl);
+    if (f32) pow2_shape_f32(kind, N, &B, &tpl, &smem);
+    else pow2_shape_f64(kind, N, &B, &tpl, &smem);
     a.B = B;
     a.LDB = B;
     a.tpl = tpl;
     a.threads = B * tpl;
     a.smem = smem;
     a.kern = kind;
-    a.persist = 0;
     a.tma = 0;
     // TMA-staged input tile for the forward ZYX store: the tile's lines must
     // be adjacent (the tensor's inner dimension) and their elements a
     // 16-byte multiple apart, past the last line
-    if (f32 && allow_tma && kind == KIND_COL_DS && !pl && N >= 256 && N <= 2048 && a.in.lstride == 1 &&
+    if (f32 && allow_tma && kind == KIND_COL_DS && N >= 256 && N <= 2048 && a.in.lstride == 1 &&
         a.in.per >= a.nlines && a.in.es % 2 == 0 && a.in.es >= a.nlines && a.gcount == 0 && (B % 2) == 0) {
         a.tma = 1;
         a.smem = pow2_tma_smem_f32(N, sym_of(a));
     }
     // bulk-copied tile for the row-style ZYX load: plain FFT lines that lie
     // one after another in memory
-    if (f32 && allow_tma && kind == KIND_COL_SD && !pl && a.op == OP_C2C && a.sign > 0 && a.n_in == N &&
+    if (f32 && allow_tma && kind == KIND_COL_SD && a.op == OP_C2C && a.sign > 0 && a.n_in == N &&
         a.in.es == 1 && a.in.lstride == N && a.in.per >= a.nlines && a.gcount == 0 && pow2_pick_zbulk_f32(N)) {
         a.tma = 2;
         a.smem = pow2_zbulk_smem_f32(N);
-    }
-    if (pl) {
-        // persistent grid: resident CTAs per SM times the SM count
-        void* fn = f32 ? pow2_pick_f32(kind, N, a.sign > 0, sym_of(a), true)
-                       : pow2_pick_f64(kind, N, a.sign > 0, sym_of(a), true);
-        int dev = 0, sms = 0, per = 0;
-        if (fn && cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, a.threads, a.smem) == cudaSuccess && per > 0) {
-            a.persist = sms * per;
-        } else {
-            cudaGetLastError();
-            return false;
-        }
     }
     return true;
 }
@@ -106,16 +89,15 @@ cudaError_t pow2_prepare()
         for (int kind = KIND_COL_DD; kind <= KIND_ROW_C2R; ++kind)
             for (int N = 64; N <= 4096; N *= 2)
                 for (int inv = 0; inv < 2; ++inv)
-                    for (int sym = 0; sym < 3; ++sym)
-                        for (int pl = 0; pl < 2; ++pl) {
-                            void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, sym, pl) : pow2_pick_f64(kind, N, inv, sym, pl);
-                            if (f == 0 && kind == KIND_COL_SD && inv && !pl && sym == 0) {
+                    for (int sym = 0; sym < 3; ++sym) {
+                            void* fn = f == 0 ? pow2_pick_f32(kind, N, inv, sym) : pow2_pick_f64(kind, N, inv, sym);
+                            if (f == 0 && kind == KIND_COL_SD && inv && sym == 0) {
                                 void* fb = pow2_pick_zbulk_f32(N);
                                 if (fb && cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                                227 * 1024) != cudaSuccess)
                                     return cudaGetLastError();
                             }
-                            if (f == 0 && kind == KIND_COL_DS && !inv && !pl) {
+                            if (f == 0 && kind == KIND_COL_DS && !inv) {
                                 void* ft = pow2_pick_tma_f32(N, sym);
                                 if (ft && cudaFuncSetAttribute(ft, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                                227 * 1024) != cudaSuccess)
@@ -131,15 +113,14 @@ cudaError_t pow2_prepare()
 
 cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
 {
-    const bool inv = a.sign > 0, pl = a.persist > 0;
+    const bool inv = a.sign > 0;
     const int sym = sym_of(a);
     void* fn = a.tma == 2 ? pow2_pick_zbulk_f32(a.nfft)
                : a.tma ? pow2_pick_tma_f32(a.nfft, sym)
-                     : (f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym, pl) : pow2_pick_f64(a.kern, a.nfft, inv, sym, pl));
+                     : (f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym) : pow2_pick_f64(a.kern, a.nfft, inv, sym));
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;
     long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;
-    if (pl && grid > a.persist) grid = a.persist;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<StageArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(a.threads), args, a.smem, st);

@@ -531,166 +531,6 @@ template <typename T, int N, int B> __host__ __device__ constexpr size_t col_tma
 }
 
 // ---------------------------------------------------------------------------
-// Persistent, software-pipelined column kernels.  Each CTA walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; while it transforms tile i out of
-// one shared-memory buffer, cp.async copies of tile i + gridDim.x's
-// first-pass inputs land in the other buffer, so HBM reads continue through
-// the compute phase instead of stopping at every tile.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
-
-template <class C> __device__ __forceinline__ void cp_async_c(C* sdst, const C* gsrc)
-{
-    if constexpr (sizeof(C) == 8) cp_async8(sdst, gsrc);
-    else cp_async16(sdst, gsrc);
-}
-
-// Issue the copies of one tile's first-pass inputs into buffer s.
-template <class C, class T, int N, int E, int B, int MODE, bool DCT>
-__device__ __forceinline__ void col_prefetch(const StageArgs& a, C* s, long long tile, int tid)
-{
-    typedef PassIdx<N, E, 0> P0;
-    typedef ColSlot<T, B, MODE != 0> S;
-    typedef EF<T, N, E, B> Ef;
-    constexpr int M = N / 2;
-    if constexpr (MODE != 2) {
-        const int l = tid % B, t = tid / B;
-        const long long L = tile * B + l;
-        if (L < a.nlines) {
-            const C* src = static_cast<const C*>(a.src) + lbase(a.in, L);
-            const long long es = a.in.es;
-#pragma unroll
-            for (int b = 0; b < P0::BM; ++b)
-#pragma unroll
-                for (int r = 0; r < P0::R; ++r) {
-                    const int K = P0::in_K(b, r);
-                    const int e = t + K;
-                    const long long off = DCT ? (long long)(e <= M ? e : N - e) * es : (long long)e * es;
-                    cp_async_c(&s[S::at_k(t, l, K, 1)], src + off);
-                }
-        }
-    } else {
-        const int le = Ef::line(tid);
-        const long long Le = tile * B + le;
-        if (Le < a.nlines) {
-            const C* src = static_cast<const C*>(a.src) + lbase(a.in, Le);
-            for (int c = Ef::chunk0(tid) * Ef::VEC; c < N; c += Ef::STEP * Ef::VEC)
-#pragma unroll
-                for (int v = 0; v < Ef::VEC; ++v) {
-                    const int e = c + v;
-                    const int ee = DCT ? (e <= M ? e : N - e) : e;
-                    cp_async_c(&s[S::at(e, le)], src + ee);
-                }
-        }
-    }
-}
-
-template <typename T, int N, int E, int B, int MODE, bool INV, bool DCT>
-__global__ void __launch_bounds__(B * (N / E), 1) col_kernel_pl(const __grid_constant__ StageArgs a)
-{
-    typedef typename CxT<T>::t C;
-    typedef P2<N, E> PL;
-    constexpr int NP = PL::NPASS;
-    constexpr bool SWZ = MODE != 0;
-    typedef ColSlot<T, B, SWZ> S;
-    typedef EF<T, N, E, B> Ef;
-    constexpr int M = N / 2;
-    constexpr int SLOTS = (cpad_c(N - 1) + 1) * B;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sbuf = reinterpret_cast<C*>(smem_raw);
-    const int tid = threadIdx.x, l = tid % B, t = tid / B;
-    const C* tw = static_cast<const C*>(a.tw);
-    const long long ntiles = (a.nlines + B - 1) / B;
-    typedef PassIdx<N, E, 0> P0;
-    typedef PassIdx<N, E, NP - 1> PLast;
-
-    long long tile = blockIdx.x;
-    if (tile < ntiles) col_prefetch<C, T, N, E, B, MODE, DCT>(a, sbuf, tile, tid);
-    cp_async_commit();
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        C* s = sbuf + (it & 1) * SLOTS;
-        const long long next = tile + gridDim.x;
-        if (next < ntiles) col_prefetch<C, T, N, E, B, MODE, DCT>(a, sbuf + ((it + 1) & 1) * SLOTS, next, tid);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const long long L = tile * B + l;
-        const bool valid = L < a.nlines;
-        C v[E];
-#pragma unroll
-        for (int b = 0; b < P0::BM; ++b)
-#pragma unroll
-            for (int r = 0; r < P0::R; ++r) {
-                const C x = s[S::at_k(t, l, P0::in_K(b, r), 1)];
-                v[b * P0::R + r] = INV ? swp(x) : x;
-            }
-        pass_compute<C, T, N, E, 0>(v, t, tw, 1);
-        ColRest<C, T, N, E, B, SWZ, 1, NP>::run(v, s, l, t, tw);
-        if constexpr (MODE != 1) {
-            if (valid) {
-                C* dst = static_cast<C*>(a.dst) + lbase(a.out, L);
-                const long long es = a.out.es;
-                const int u = PLast::out_u(t);
-#pragma unroll
-                for (int b = 0; b < PLast::BM; ++b)
-#pragma unroll
-                    for (int r = 0; r < PLast::R; ++r) {
-                        const int e = u + PLast::out_K(b, r);
-                        const C x = v[b * PLast::R + r];
-                        if (!DCT || e <= M) dst[(long long)e * es] = INV ? swp(x) : x;
-                    }
-            }
-        } else {
-            __syncthreads();
-            {
-                const int u = PLast::out_u(t);
-#pragma unroll
-                for (int b = 0; b < PLast::BM; ++b)
-#pragma unroll
-                    for (int r = 0; r < PLast::R; ++r)
-                        s[S::at_k(u, l, PLast::out_K(b, r), PLast::OUT_UA)] = v[b * PLast::R + r];
-            }
-            __syncthreads();
-            const int le = Ef::line(tid);
-            const long long Le = tile * B + le;
-            if (Le < a.nlines) {
-                C* dst = static_cast<C*>(a.dst) + lbase(a.out, Le);
-                if constexpr (DCT || Ef::VEC == 1) {
-                    for (int c = Ef::chunk0(tid); c < (DCT ? M + 1 : N); c += Ef::STEP) {
-                        const C x = s[S::at(c, le)];
-                        dst[c] = INV ? swp(x) : x;
-                    }
-                } else {
-                    typedef typename Vec4<T>::t V;
-                    V* dst4 = reinterpret_cast<V*>(dst);
-                    for (int c = Ef::chunk0(tid); c < N / 2; c += Ef::STEP) {
-                        C x0 = s[S::at(2 * c, le)], x1 = s[S::at(2 * c + 1, le)];
-                        if (INV) {
-                            x0 = swp(x0);
-                            x1 = swp(x1);
-                        }
-                        dst4[c] = V{x0.x, x0.y, x1.x, x1.y};
-                    }
-                }
-            }
-        }
-        __syncthreads();  // buffer s is refilled by the prefetch of the next iteration
-    }
-    cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
 // Row kernels: X stage, Nx = 2N real points per row, H = N + 1 bins; row
 // L starts at L * lstride of its array (real rows may be padded).
 // OPR 0: r2c (forward), OPR 1: c2r (inverse).
@@ -990,24 +830,9 @@ template <typename T> __host__ __device__ constexpr int col_B(int N)
     return sizeof(T) == 4 ? (N <= 64 ? 64 : N <= 128 ? 32 : N <= 256 ? 16 : N <= 2048 ? 8 : 4)
                           : (N <= 64 ? 64 : N <= 128 ? 32 : N <= 256 ? 16 : N <= 512 ? 8 : N <= 2048 ? 4 : 2);
 }
-// Pipelined persistent column kernels: the FP32 ZYX-load kernel (MODE 2) of
-// 512 / 1024 points, where the copies of the next tile hide the latency of
-// its element-contiguous reads; the other modes run faster as two resident
-// one-tile CTAs per SM.
-#ifndef P3_PIPELINE
-#define P3_PIPELINE 1
-#endif
-#ifndef P3_PL_E
-#define P3_PL_E 16
-#endif
-template <typename T> __host__ __device__ constexpr bool col_zrow(int N);
-template <typename T> __host__ __device__ constexpr bool col_pipelined(int N, int mode)
-{
-    return P3_PIPELINE && sizeof(T) == 4 && mode == 2 && N >= 512 && N <= 1024 && !col_zrow<T>(N);
-}
-template <typename T> __host__ __device__ constexpr int col_pl_E(int N, int mode) { return mode == 2 ? 16 : P3_PL_E; }
-// Row-style ZYX-load kernel for FP32 lines of 256 .. 1024 points (a line's
-// threads fit in one warp); it takes precedence over the pipelined one.
+
+// Row-style ZYX-load kernel for FP32 lines of 256 .. 2048 points (a line's
+// threads fit in one warp up to 1024 points; two warps at 2048).
 #ifndef P3_ZROW
 #define P3_ZROW 1
 #endif

@@ -10,13 +10,6 @@ template <int N, int MODE, bool INV, int SYM> void* col_fn()
 {
     return (void*)col_kernel<double, N, col_E<double>(N, MODE), col_B<double>(N), MODE, INV, SYM>;
 }
-template <int N, int MODE, bool INV, int SYM> void* col_pl_fn()
-{
-    if constexpr (SYM != 2 && col_pipelined<double>(N, MODE))
-        return (void*)col_kernel_pl<double, N, col_pl_E<double>(N, MODE), col_B<double>(N), MODE, INV, SYM == 1>;
-    else
-        return nullptr;
-}
 template <int N, bool INV, int SYM> void* zrow_fn()
 {
     if constexpr (col_zrow<double>(N))
@@ -31,44 +24,42 @@ template <int N, int OPR> void* row_fn() { return (void*)row_kernel<double, N, r
     (sym == 2 ? (inv ? (void*)nullptr : FN<N, MODE, false, 2>()) \
      : inv ? (sym ? FN<N, MODE, true, 1>() : FN<N, MODE, true, 0>()) \
            : (sym ? FN<N, MODE, false, 1>() : FN<N, MODE, false, 0>()))
-template <int N> void* pick_n(int kind, bool inv, int sym, bool pl)
+template <int N> void* pick_n(int kind, bool inv, int sym)
 {
     switch (kind) {
-    case KIND_COL_DD: return pl ? P3_COL_PICK(col_pl_fn, 0) : P3_COL_PICK(col_fn, 0);
-    case KIND_COL_DS: return pl ? P3_COL_PICK(col_pl_fn, 1) : P3_COL_PICK(col_fn, 1);
+    case KIND_COL_DD: return P3_COL_PICK(col_fn, 0);
+    case KIND_COL_DS: return P3_COL_PICK(col_fn, 1);
     case KIND_COL_SD:
         if (col_zrow<double>(N))
-            return pl ? nullptr
-                      : (sym == 2 ? (inv ? (void*)nullptr : zrow_fn<N, false, 2>())
-                         : inv ? (sym ? zrow_fn<N, true, 1>() : zrow_fn<N, true, 0>())
-                               : (sym ? zrow_fn<N, false, 1>() : zrow_fn<N, false, 0>()));
-        return pl ? P3_COL_PICK(col_pl_fn, 2) : P3_COL_PICK(col_fn, 2);
-    case KIND_ROW_R2C: return pl ? nullptr : row_fn<N, 0>();
-    case KIND_ROW_C2R: return pl ? nullptr : row_fn<N, 1>();
+            return sym == 2 ? (inv ? (void*)nullptr : zrow_fn<N, false, 2>())
+                   : inv ? (sym ? zrow_fn<N, true, 1>() : zrow_fn<N, true, 0>())
+                         : (sym ? zrow_fn<N, false, 1>() : zrow_fn<N, false, 0>());
+        return P3_COL_PICK(col_fn, 2);
+    case KIND_ROW_R2C: return row_fn<N, 0>();
+    case KIND_ROW_C2R: return row_fn<N, 1>();
     default: return nullptr;
     }
 }
 #undef P3_COL_PICK
 }  // namespace
 
-void* pow2_pick_f64(int kind, int N, bool inv, int sym, bool pl)
+void* pow2_pick_f64(int kind, int N, bool inv, int sym)
 {
     switch (N) {
-    case 64: return pick_n<64>(kind, inv, sym, pl);
-    case 128: return pick_n<128>(kind, inv, sym, pl);
-    case 256: return pick_n<256>(kind, inv, sym, pl);
-    case 512: return pick_n<512>(kind, inv, sym, pl);
-    case 1024: return pick_n<1024>(kind, inv, sym, pl);
-    case 2048: return pick_n<2048>(kind, inv, sym, pl);
-    case 4096: return pick_n<4096>(kind, inv, sym, pl);
+    case 64: return pick_n<64>(kind, inv, sym);
+    case 128: return pick_n<128>(kind, inv, sym);
+    case 256: return pick_n<256>(kind, inv, sym);
+    case 512: return pick_n<512>(kind, inv, sym);
+    case 1024: return pick_n<1024>(kind, inv, sym);
+    case 2048: return pick_n<2048>(kind, inv, sym);
+    case 4096: return pick_n<4096>(kind, inv, sym);
     default: return nullptr;
     }
 }
 
-void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* smem, int* pl)
+void pow2_shape_f64(int kind, int N, int* B, int* tpl, size_t* smem)
 {
     using namespace pw;
-    *pl = 0;
     if (kind == KIND_ROW_R2C || kind == KIND_ROW_C2R) {
         const int E = row_E<double>(N);
         *B = row_B<double>(N);
@@ -87,14 +78,8 @@ void pow2_shape_f64(int kind, int N, bool allow_pl, int* B, int* tpl, size_t* sm
         const int mode = kind == KIND_COL_SD ? 2 : kind == KIND_COL_DS ? 1 : 0;
         *B = col_B<double>(N);
         const size_t slots = (size_t)(cpad_c(N - 1) + 1) * (size_t)(*B);
-        if (allow_pl && col_pipelined<double>(N, mode)) {
-            *pl = 1;
-            *tpl = N / col_pl_E<double>(N, mode);
-            *smem = 2 * slots * sizeof(double) * 2;
-        } else {
-            *tpl = N / col_E<double>(N, mode);
-            *smem = slots * sizeof(double) * 2;
-        }
+        *tpl = N / col_E<double>(N, mode);
+        *smem = slots * sizeof(double) * 2;
     }
 }
 
