@@ -224,8 +224,19 @@ __device__ __forceinline__ void store_value(const StageArgs& a, const C* sl, int
     }
 }
 
+// Resident CTAs per SM the register allocation is sized for.  FP32: four
+// 256-thread CTAs (64 registers, a few bytes of spill) hide the strided loads
+// and stores of the generic path better than two CTAs at 96 registers (about
+// 20 % faster on 7-smooth grids); five gain nothing more.  FP64 stays at two:
+// three CTAs spill several hundred bytes for a gain of about 2 %.
+#ifndef P3_GEN_MINB
+#define P3_GEN_MINB 4
+#endif
+#ifndef P3_GEN_MINB_F64
+#define P3_GEN_MINB_F64 2
+#endif
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads, 2) stage_kernel(const __grid_constant__ StageArgs a)
+__global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P3_GEN_MINB_F64)) stage_kernel(const __grid_constant__ StageArgs a)
 {
     typedef typename Cx<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
