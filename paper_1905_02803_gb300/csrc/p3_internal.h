@@ -12,8 +12,12 @@ namespace p3 {
 // Largest radix sequence a line plan can hold (mixed 2/3/5/7 factorizations
 // of lengths <= 4096 have at most 12 prime factors).
 constexpr int kMaxPasses = 14;
-// Complex values each thread keeps in registers during a pass.
-constexpr int kVmax = 16;
+// Generic kernel: about this many points of a line per thread (threads per
+// line = ceil(n / kVmax); the pass loops take any count).
+#ifndef P3_GEN_VMAX
+#define P3_GEN_VMAX 16
+#endif
+constexpr int kVmax = P3_GEN_VMAX;
 // Threads per CTA never exceed this (matches __launch_bounds__).
 constexpr int kMaxThreads = 256;
 // Longest native line; Bluestein lines need a padded length <= this too.
