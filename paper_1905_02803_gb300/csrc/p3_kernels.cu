@@ -171,6 +171,41 @@ __device__ __forceinline__ C load_value(const StageArgs& a, long long base, int 
     return v;
 }
 
+// Ops whose load is a plain copy of one complex value (no pre-processing
+// beyond the inverse's real/imaginary swap): their tiles are filled by
+// asynchronous copies straight into shared memory, all of a thread's copies
+// in flight at once and no registers held for them.
+#ifndef P3_GEN_CPASYNC
+#define P3_GEN_CPASYNC 1
+#endif
+__device__ __forceinline__ bool direct_load(const StageArgs& a)
+{
+    return P3_GEN_CPASYNC && !a.blue &&
+           (a.op == OP_C2C || a.op == OP_COPY || a.op == OP_R2C_HALF || a.op == OP_C2R_HALF);
+}
+
+template <class C, class T>
+__device__ __forceinline__ const C* direct_src(const StageArgs& a, long long base, int e)
+{
+    if (a.op == OP_R2C_HALF) return reinterpret_cast<const C*>(static_cast<const T*>(a.src) + base + 2 * (long long)e);
+    return static_cast<const C*>(a.src) + base + (long long)e * a.in.es;
+}
+
+template <class C>
+__device__ __forceinline__ void copy_async(C* dst, const C* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void copy_async_wait()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Transform result for bin k of the line whose slots start at sl (stride LDB).
 template <class C>
 __device__ __forceinline__ C result(const StageArgs& a, const C* sl, int LDB, int k)
@@ -254,7 +289,75 @@ __global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P
     // their latencies overlap instead of adding up
     constexpr int KB = sizeof(T) == 4 ? 8 : 4;
     const C zero = mk<C>((T)0, (T)0);
-    if (a.in_elem_fast) {
+    if (direct_load(a)) {
+        // every slot is a copy of one input value (nfill == nload); the
+        // thread's own copies are complete after the wait, so it applies the
+        // inverse's swap to exactly those slots before the barrier.  The c2r
+        // input F[0..n] is copied as it is (F[n] to the second buffer, unused
+        // until the first pass) and pre-twiddled in shared memory below.
+        const bool sw = a.sign > 0 && (a.op == OP_C2C || a.op == OP_COPY);
+        if (a.in_elem_fast) {
+            const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+            const int ncopy = a.op == OP_C2R_HALF ? nload + 1 : nload;
+            for (int l = warp; l < B; l += nw) {
+                const long long L = L0 + l;
+                if (L >= a.nlines) break;
+                const long long base = line_base(a.in, L);
+                for (int e = lane; e < ncopy; e += 32)
+                    copy_async(e < nload ? s0 + (size_t)e * LDB + l : s1 + l, direct_src<C, T>(a, base, e));
+            }
+            copy_async_wait();
+            if (sw)
+                for (int l = warp; l < B; l += nw) {
+                    if (L0 + l >= a.nlines) break;
+                    for (int e = lane; e < nload; e += 32) s0[(size_t)e * LDB + l] = swp(s0[(size_t)e * LDB + l]);
+                }
+        } else {
+            const int l = tid & (B - 1);
+            const long long L = L0 + l;
+            const int st = NT / B;
+            if (L < a.nlines) {
+                const long long base = line_base(a.in, L);
+                for (int e = tid / B; e < nload; e += st) copy_async(s0 + (size_t)e * LDB + l, direct_src<C, T>(a, base, e));
+                copy_async_wait();
+                if (sw)
+                    for (int e = tid / B; e < nload; e += st) s0[(size_t)e * LDB + l] = swp(s0[(size_t)e * LDB + l]);
+                if (a.op == OP_C2R_HALF && tid < B) copy_async(s1 + l, direct_src<C, T>(a, base, nload));
+                copy_async_wait();
+            }
+        }
+        if (a.op == OP_C2R_HALF) {
+            // Z[k] = (F[k] + conj F[n-k]) + i (F[k] - conj F[n-k]) exp(+2 pi i k / Nx)
+            // (imaginary parts of F[0] and F[n] dropped), swapped for the
+            // inverse FFT; the pair k, n - k is done by one thread, in place
+            __syncthreads();
+            const int n = a.nfft, half = n / 2 + 1;
+            const C* tw2 = static_cast<const C*>(a.tw2);
+            for (int i = tid; i < B * half; i += NT) {
+                const int l = i & (B - 1), k = i / B;
+                if (L0 + l >= a.nlines) continue;
+                const int m = n - k;  // partner slot (F[n] for k = 0)
+                C Fk = s0[(size_t)k * LDB + l];
+                C Fm = k == 0 ? s1[l] : s0[(size_t)m * LDB + l];
+                if (k == 0) {
+                    Fk.y = (T)0;
+                    Fm.y = (T)0;
+                }
+                {
+                    const C B_ = cnj(Fm);
+                    const C ze = add(Fk, B_);
+                    const C zo = mul(sub(Fk, B_), cnj(ldg(tw2 + k)));
+                    s0[(size_t)k * LDB + l] = swp(mk<C>(ze.x - zo.y, ze.y + zo.x));
+                }
+                if (k > 0 && m != k) {
+                    const C B_ = cnj(Fk);
+                    const C ze = add(Fm, B_);
+                    const C zo = mul(sub(Fm, B_), cnj(ldg(tw2 + m)));
+                    s0[(size_t)m * LDB + l] = swp(mk<C>(ze.x - zo.y, ze.y + zo.x));
+                }
+            }
+        }
+    } else if (a.in_elem_fast) {
         const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
         for (int l = warp; l < B; l += nw) {
             const long long L = L0 + l;
