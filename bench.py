@@ -259,6 +259,9 @@ def main():
                     help="with --report: only these comma-separated configs (names in REPORT_CONFIGS, or batch64)")
     ap.add_argument("--grid", default="1024",
                     help="grid edge N, or NX,NY,NZ (1024 is the benchmark workload; others are for profiling)")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="time the FP64 CPU oracle's full forward + inverse pair at the small configurations, "
+                         "on all host threads and on one (no GPU use)")
     args = ap.parse_args()
     global NX, NY, NZ
     g = [int(v) for v in str(args.grid).split(",")]
@@ -269,6 +272,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.cpu_report:
+        run_cpu_report()
         return
     if args.report:
         run_report(args)
@@ -705,6 +711,38 @@ def _report_batch(steps, warmup, nstreams=16):
             "ms_batch_streams": round(ms_batch, 4), "ms_batch_streams_cuda_graph": round(ms_batch_graph, 4),
             "batch_streams": nstreams, "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
             "hbm_roofline_frac": round(roof_ms / best, 4), "launches_per_step": launches, "kernels": kinds}
+
+
+CPU_REPORT_CONFIGS = [
+    # name, (nx, ny, nz), oracle transform types, single-thread run too
+    ("32cube_f64", (32, 32, 32), (0, 0, 0), True),
+    ("256cube_f64", (256, 256, 256), (0, 0, 0), True),
+    ("512cube_f64", (512, 512, 512), (0, 0, 0), False),
+    ("channel_480x360x257_f64", (480, 360, 257), (0, 0, 1), False),
+]
+
+
+def run_cpu_report():
+    """The CPU baseline at the small configurations: the FP64 oracle's whole
+    forward + inverse pair (not a line sample), best of three (one at 512^3
+    and for the channel grid), on every host thread and, where it stays short,
+    on one.  One JSON line per configuration and thread count."""
+    import oracle as O
+    from paper_1905_02803_gb300 import inputs
+
+    for name, (nx, ny, nz), tt, single in CPU_REPORT_CONFIGS:
+        f = inputs.uniform_field((nz, ny, nx), 1)
+        reps = 3 if nx * ny * nz <= 256 ** 3 else 1
+        for nthreads in ([0, 1] if single else [0]):
+            best = None
+            for _ in range(reps):
+                t = time.perf_counter()
+                F = O.forward(f, tt, nthreads=nthreads)
+                O.backward(F, nx, tt, nthreads=nthreads)
+                dt = time.perf_counter() - t
+                best = dt if best is None else min(best, dt)
+            print(json.dumps({"config": name, "grid": [nx, ny, nz], "kind": "oracle", "cpu_ms": round(best * 1e3, 3),
+                              "threads": nthreads or O.nthreads_default(), "reps": reps}), flush=True)
 
 
 def run_report(args):
