@@ -354,11 +354,16 @@ const char* kern_name(int k, int tc, int tma = 0)
     }
 }
 
-bool smooth_or_small(int n)
+// Whether a line of n points has a kernel: n <= 1, or a 2/3/5/7-smooth n up
+// to the longest native line, or a Bluestein length whose padded transform
+// fits.  n is 64-bit so that the extended lengths 2(Nz - 1) and 2(Nz + 1)
+// of the Chebyshev and sine transforms cannot wrap for any int Nz.
+bool smooth_or_small(long long n)
 {
     std::vector<int> r;
     if (n <= 1) return true;
-    if (factor(n, r)) return n <= p3::kMaxLine;
+    if (n > p3::kMaxLine) return false;  // longer than any native or Bluestein-padded line
+    if (factor((int)n, r)) return true;
     return pow2_ceil(2LL * n - 1) <= p3::kMaxLine;
 }
 
@@ -507,8 +512,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     if (!smooth_or_small(nx % 2 == 0 ? nx / 2 : nx)) return P3_ERR_UNSUPPORTED;
     if (ttype[1] == P3_FFT && !smooth_or_small(ny)) return P3_ERR_UNSUPPORTED;
     if (ttype[2] == P3_FFT && !smooth_or_small(nz)) return P3_ERR_UNSUPPORTED;
-    if (ttype[2] == P3_CHEB && !smooth_or_small(2 * (nz - 1))) return P3_ERR_UNSUPPORTED;
-    if (ttype[2] == P3_SINE && !smooth_or_small(2 * (nz + 1))) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_CHEB && !smooth_or_small(2LL * (nz - 1))) return P3_ERR_UNSUPPORTED;
+    if (ttype[2] == P3_SINE && !smooth_or_small(2LL * ((long long)nz + 1))) return P3_ERR_UNSUPPORTED;
 
     p3_plan P = new (std::nothrow) p3_plan_s();
     if (!P) return P3_ERR_NOMEM;

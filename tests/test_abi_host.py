@@ -73,6 +73,12 @@ FFT3 = (P.P3_FFT, P.P3_FFT, P.P3_FFT)
     ((8, 8192, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
     ((8, 8, 2053, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),   # prime > 2048
     ((2 * 4099, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    # extended third-dimension lengths 2(Nz - 1) / 2(Nz + 1) beyond int range
+    ((8, 8, 2 ** 31 - 1, P.P3_F32, (P.P3_FFT, P.P3_FFT, P.P3_SINE), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    ((8, 8, 2 ** 31 - 1, P.P3_F64, (P.P3_FFT, P.P3_FFT, P.P3_CHEB), P.P3_LAYOUT_XYZ, 0), P.P3_ERR_UNSUPPORTED),
+    ((8, 8, 2 ** 30 + 1, P.P3_F64, (P.P3_FFT, P.P3_FFT, P.P3_CHEB), P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    ((8, 8, 2 ** 31 - 1, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
+    ((2 ** 31 - 1, 8, 8, P.P3_F32, FFT3, P.P3_LAYOUT_ZYX, 0), P.P3_ERR_UNSUPPORTED),
 ])
 def test_plan_create_rejects_before_cuda(lib, args, expect):
     st, h = P.p3_plan_create(*args, check=False)
