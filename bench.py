@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -82,7 +83,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        # raw samples: the system temporary directory unless P3_BENCH_CLOCKS_DIR
+        # names another (the JSON line carries their summary either way)
+        out_dir = os.environ.get("P3_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
