@@ -520,7 +520,7 @@ def main():
 
 # ---------------------------------------------------------------------------
 # --report: every benchmark configuration, one JSON line each (not the
-# driver's single-line contract; used to fill profiles/configs_report.md)
+# default single-line benchmark output; used to fill profiles/configs_report.md)
 # ---------------------------------------------------------------------------
 REPORT_CONFIGS = [
     # name, (nx, ny, nz), precision, ttypes, layout, input

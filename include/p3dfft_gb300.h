@@ -61,7 +61,7 @@ typedef struct p3_plan_s* p3_plan;
 typedef enum {
     P3_OK = 0,
     P3_ERR_INVALID = 1,     /* bad argument: NULL, misaligned, bad dims, overlap */
-    P3_ERR_UNSUPPORTED = 2, /* valid request outside what this build implements */
+    P3_ERR_UNSUPPORTED = 2, /* valid request outside what this library implements */
     P3_ERR_NOMEM = 3,       /* host or device allocation at plan creation failed */
     P3_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
     P3_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
