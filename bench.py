@@ -136,7 +136,7 @@ class ClockSampler:
 
 def cpu_oracle_sample(frac, nthreads=0):
     """Time the FP64 oracle's stage functions on the first `frac` of the lines
-    of every stage of the 1024^3 pair (full-size strides; buffers are
+    of every stage of the grid's pair (full-size strides; buffers are
     allocated lazily and only sampled lines are touched), scaled to all lines.
     Returns (estimated ms per fwd+inv pair, threads, description)."""
     import numpy as np
@@ -147,6 +147,10 @@ def cpu_oracle_sample(frac, nthreads=0):
     nx, ny, nz = NX, NY, NZ
     H = nx // 2 + 1
     nthreads = nthreads or O.nthreads_default()
+    # at least 2^24 points' worth of lines per stage (the whole grid below
+    # that), so that starting the oracle's threads stays a small part of
+    # each timed call; 1024^3 samples 1/64 of its lines or more
+    frac = min(1.0, max(frac, float(1 << 24) / (nx * ny * nz)))
     rows = ny * nz
     ylines = H * nz
     zlines = H * ny
