@@ -12,6 +12,7 @@ Transform types per dimension: FFT, CHEB (DCT-I, third dimension only), EMPTY,
 SINE (DST-I, third dimension only).
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -202,3 +203,78 @@ def backward_rows(g, nx):
     out = np.zeros((G.shape[0], nx))
     x_c2r_rows(nx, G.reshape(-1), out.reshape(-1), 0, G.shape[0])
     return out
+
+
+# --- whole sampled planes of the output on full-size grids -----------------
+
+def forward_kx_planes(chunks, nx, ny, nz, kxs, nthreads=0):
+    """Forward output planes F[kx][ky][kz] (ZYX order: one [Ny][Nz] plane per
+    requested kx) of a real [Nz][Ny][Nx] field fed as (z0, block) z-chunks in
+    order.  The stages are the definition's three passes (Sect. 2): the X
+    real-to-complex transform of every row (oracle rows), keeping bins kxs;
+    then the Y and Z complex transforms of those planes (oracle lines)."""
+    kxs = np.asarray(kxs, dtype=np.int64)
+    H = half(nx)
+    if np.any(kxs < 0) or np.any(kxs >= H):
+        raise ValueError("kx outside the half spectrum")
+    nk = len(kxs)
+    G = np.empty((nk, nz, ny), dtype=np.complex128)  # [k][z][y]
+    zdone = 0
+    for z0, block in chunks:
+        block = np.ascontiguousarray(block, dtype=np.float64)
+        zc = block.shape[0]
+        if z0 != zdone or block.shape[1:] != (ny, nx):
+            raise ValueError("chunks must cover z in order with [zc][Ny][Nx] blocks")
+        F = np.empty(zc * ny * H, dtype=np.complex128)
+        x_r2c_rows(nx, block.reshape(-1), F, 0, zc * ny, nthreads)
+        G[:, z0:z0 + zc, :] = F.reshape(zc, ny, H)[:, :, kxs].transpose(2, 0, 1)
+        zdone += zc
+    if zdone != nz:
+        raise ValueError("chunks cover %d of %d planes" % (zdone, nz))
+    flat = G.reshape(-1)
+    if ny > 1:  # Y lines: line L = k * nz + z at L * ny, unit stride
+        c2c_lines(ny, nk * nz, 0, ny, 1, flat, 0, nk * nz, -1, nthreads)
+    if nz > 1:  # Z lines: line L = k * ny + y at k * nz * ny + y, stride ny
+        c2c_lines(nz, ny, nz * ny, 1, ny, flat, 0, nk * ny, -1, nthreads)
+    return np.ascontiguousarray(G.transpose(0, 2, 1))  # [k][ky][kz]
+
+
+def inverse_z_table(nz, zs, sign=+1):
+    """T[kz][j] = exp(sign 2 pi i kz zs[j] / Nz), the product kz * z reduced
+    mod Nz exactly in integers before the FP64 cos / sin."""
+    kz = np.arange(nz, dtype=np.int64)
+    t = np.mod(np.outer(kz, np.asarray(zs, dtype=np.int64)), nz).astype(np.float64)
+    ang = 2.0 * math.pi * t / nz
+    return np.cos(ang) + sign * 1j * np.sin(ang)
+
+
+def backward_z_planes(chunks, nx, ny, nz, zs, nthreads=0):
+    """Inverse output planes f[z][y][x] for the requested z of a complex ZYX
+    input [H][Ny][Nz] fed as (kx0, block) kx-chunks in order.  The inverse Z
+    transform is the definition sum sum_kz F[kx][ky][kz] exp(+2 pi i kz z/Nz)
+    evaluated at those z only (a matrix product with exact-index roots of
+    unity); the inverse Y transform (oracle lines) and the weighted c2r of
+    every row (oracle rows, Sect. 3.2 reading of the redundant bins) finish
+    each plane."""
+    zs = np.asarray(zs, dtype=np.int64)
+    H = half(nx)
+    nzs = len(zs)
+    T = inverse_z_table(nz, zs)
+    Q = np.empty((nzs, ny, H), dtype=np.complex128)  # [j][y][kx]
+    kdone = 0
+    for k0, block in chunks:
+        block = np.ascontiguousarray(block, dtype=np.complex128)
+        kc = block.shape[0]
+        if k0 != kdone or block.shape[1:] != (ny, nz):
+            raise ValueError("chunks must cover kx in order with [kc][Ny][Nz] blocks")
+        A = block.reshape(kc * ny, nz) @ T  # [(k, y)][j]
+        Q[:, :, k0:k0 + kc] = A.reshape(kc, ny, nzs).transpose(2, 1, 0)
+        kdone += kc
+    if kdone != H:
+        raise ValueError("chunks cover %d of %d kx planes" % (kdone, H))
+    flat = Q.reshape(-1)
+    if ny > 1:  # Y lines: line L = j * H + kx at j * ny * H + kx, stride H
+        c2c_lines(ny, H, ny * H, 1, H, flat, 0, nzs * H, +1, nthreads)
+    out = np.empty(nzs * ny * nx, dtype=np.float64)
+    x_c2r_rows(nx, flat, out, 0, nzs * ny, nthreads)
+    return out.reshape(nzs, ny, nx)

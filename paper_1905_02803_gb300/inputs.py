@@ -21,6 +21,14 @@ Fields (all real, C row-major [Nz][Ny][Nx]):
                      points z_j = cos(pi j / (Nz-1)), n <= Nz-1 (always with
                      n = 0 and n = Nz-1), plus 1e-3 uniform noise
   gaussian_field     i.i.d. N(0, 1)
+  uniform_field_device  uniform_field evaluated by torch on a device (or the
+                     host), bit-identical to the numpy form, in z-chunks
+  power_law_half_spectrum  seeded half-spectrum [Nz][Ny][Nx/2+1] with power
+                     |k|^slope per bin (k on signed wavenumbers), uniform
+                     phases, zero mean (a random-phase Gaussian random field
+                     once transformed to real space, which this module does
+                     not do)
+  plane_waves        16 random-amplitude plane waves
 """
 from __future__ import annotations
 
@@ -177,6 +185,17 @@ def config1_field(n: int = 32, seed: int = 0):
     return r + w, r, w
 
 
+def _wave_params(shape, seed: int, n_waves: int):
+    """Plane waves: A ~ U[0,1), integer k in [-N/4, N/4] per axis (x, y, z
+    columns), phase ~ U[0, 2 pi)."""
+    nz, ny, nx = shape
+    wa = uniform(seed, 20, n_waves)
+    wk = np.stack([randint(seed, 21 + i, n_waves, -(s // 4), s // 4)
+                   for i, s in enumerate((nx, ny, nz))], axis=1)
+    wphi = 2.0 * math.pi * uniform(seed, 24, n_waves)
+    return wa, wk, wphi
+
+
 def _turbulence_modes(shape, seed: int, n_modes: int, n_waves: int):
     nz, ny, nx = shape
     kmax = max(1.0, min(nx, ny, nz) / 2.0)
@@ -191,11 +210,7 @@ def _turbulence_modes(shape, seed: int, n_modes: int, n_waves: int):
     kn = np.linalg.norm(k.astype(np.float64), axis=1)
     amp = kn ** (-1.0 / 3.0)
     phi = 2.0 * math.pi * uniform(seed, 13, n_modes)
-    # 16 plane waves: A ~ U[0,1), k in [-N/4, N/4]^3, phase ~ U[0, 2 pi)
-    wa = uniform(seed, 20, n_waves)
-    wk = np.stack([randint(seed, 21 + i, n_waves, -(s // 4), s // 4)
-                   for i, s in enumerate((nx, ny, nz))], axis=1)
-    wphi = 2.0 * math.pi * uniform(seed, 24, n_waves)
+    wa, wk, wphi = _wave_params(shape, seed, n_waves)
     K = np.concatenate([k, wk], axis=0)
     A = np.concatenate([amp, wa])
     P = np.concatenate([phi, wphi])
@@ -283,3 +298,86 @@ def batch_dims(seed: int = 0, count: int = 64, lo: int = 48, hi: int = 384):
     sizes = np.array(smooth7_sizes(lo, hi), dtype=np.int64)
     idx = randint(seed, 40, 3 * count, 0, len(sizes) - 1).reshape(count, 3)
     return [tuple(int(sizes[i]) for i in row) for row in idx]
+
+
+# ---------------------------------------------------------------------------
+# The counter-based generator on a torch device (large grids)
+# ---------------------------------------------------------------------------
+
+def _i64(v: int) -> int:
+    """A 64-bit pattern as the signed value torch's int64 holds."""
+    v &= (1 << 64) - 1
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _srl(z, s: int):
+    """Logical right shift of int64 bit patterns (torch's >> is arithmetic)."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def _mix_torch(z):
+    z = (z ^ _srl(z, 30)) * _i64(int(_M1))
+    z = (z ^ _srl(z, 27)) * _i64(int(_M2))
+    return z ^ _srl(z, 31)
+
+
+def uniform_torch(seed: int, stream: int, start: int, count: int, device=None):
+    """U[0, 1) doubles start .. start+count-1 of one stream, as a torch FP64
+    tensor on `device`: the numpy generator's values, computed with
+    wrap-around int64 arithmetic."""
+    import torch
+    key = _i64(int(_key(seed, stream)))
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = _mix_torch(idx * _i64(int(_GAMMA)) + key)
+    return _srl(z, 11).to(torch.float64) * (2.0 ** -53)
+
+
+def uniform_field_device(shape, seed: int = 0, lo: float = -1.0, hi: float = 1.0, stream: int = 1,
+                         device=None, dtype=np.float32, zchunk: int = 0):
+    """uniform_field(shape, seed, lo, hi, stream) as a torch tensor of `dtype`
+    on `device`, generated there z-plane chunk by chunk (the same values the
+    numpy form gives, rounded once to dtype)."""
+    import torch
+    tdt = {np.float32: torch.float32, np.float64: torch.float64}[np.dtype(dtype).type]
+    nz, ny, nx = shape
+    plane = ny * nx
+    out = torch.empty(shape, dtype=tdt, device=device)
+    zc = zchunk or max(1, (1 << 27) // max(1, plane))
+    for z0 in range(0, nz, zc):
+        z1 = min(nz, z0 + zc)
+        u = uniform_torch(seed, stream, z0 * plane, (z1 - z0) * plane, device=device)
+        out[z0:z1] = (lo + (hi - lo) * u).view(z1 - z0, ny, nx).to(tdt)
+        del u
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Spectral-space draws (the caller takes them to real space)
+# ---------------------------------------------------------------------------
+
+def power_law_half_spectrum(shape, seed: int = 0, slope: float = -5.0 / 3.0) -> np.ndarray:
+    """Half-spectrum S[kz][ky][kx], kx < Nx/2 + 1, with |S|^2 = |k|^slope
+    (|k| the length of the signed wavenumber vector (kx, ky', kz'), ky' and
+    kz' folded into [-N/2, N/2)), uniform random phases from the seed, and
+    S = 0 at k = 0.  Every bin is non-zero: a dense spectrum."""
+    nz, ny, nx = shape
+    H = nx // 2 + 1
+    ky = np.fft.fftfreq(ny) * ny
+    kz = np.fft.fftfreq(nz) * nz
+    kx = np.arange(H, dtype=np.float64)
+    k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    with np.errstate(divide="ignore"):
+        amp = np.where(k2 > 0, k2 ** (slope / 4.0), 0.0)
+    phi = 2.0 * math.pi * uniform(seed, 50, nz * ny * H).reshape(nz, ny, H)
+    return amp * np.exp(1j * phi)
+
+
+def plane_waves(shape, seed: int = 0, n_waves: int = 16, dtype=np.float64, device=None):
+    """sum_i A_i cos(2 pi (k_i . x) / N + phi_i), A_i ~ U[0, 1), integer k_i
+    in [-N/4, N/4]^3 per axis, phi_i ~ U[0, 2 pi)."""
+    nz, ny, nx = shape
+    wa, wk, wphi = _wave_params(shape, seed, n_waves)
+    ex = _phase_table(nx, wk[:, 0])
+    ey = _phase_table(ny, wk[:, 1])
+    ez = _phase_table(nz, wk[:, 2]) * (wa * np.exp(1j * wphi))[:, None]
+    return _rank_sum(ez, ey, ex, device=device, dtype=dtype)

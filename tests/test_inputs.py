@@ -51,3 +51,34 @@ def test_smooth7_sizes_and_batch():
     assert s[0] == 48 and s[-1] == 384
     dims = inputs.batch_dims(0)
     assert len(dims) == 64 and all(d in s for t in dims for d in t)
+
+
+def test_device_generator_matches_the_numpy_one():
+    """The torch form of the counter-based generator (used for full-size grids
+    on the GPU) gives the numpy form's values bit for bit (here on the host)."""
+    torch = __import__("pytest").importorskip("torch")
+    a = inputs.uniform_field((5, 7, 9), 4, stream=2)
+    b = inputs.uniform_field_device((5, 7, 9), 4, stream=2, device="cpu", dtype=np.float64, zchunk=2)
+    assert isinstance(b, torch.Tensor) and np.array_equal(a, b.numpy())
+    u = inputs.uniform(9, 3, 500, start=(1 << 33) + 7)
+    v = inputs.uniform_torch(9, 3, (1 << 33) + 7, 500).numpy()
+    assert np.array_equal(u, v)
+
+
+def test_power_law_half_spectrum():
+    S = inputs.power_law_half_spectrum((8, 6, 10), 3)
+    assert S.shape == (8, 6, 6) and S[0, 0, 0] == 0
+    assert np.all(np.abs(S.ravel()[1:]) > 0)  # dense
+    # |S|^2 = |k|^(-5/3): (kx, ky, kz) = (3, -2, 1) sits at [1][4][3]
+    k2 = 9 + 4 + 1
+    assert math.isclose(abs(S[1, 4, 3]) ** 2, k2 ** (-5.0 / 6.0), rel_tol=1e-12)
+    assert np.array_equal(S, inputs.power_law_half_spectrum((8, 6, 10), 3))
+
+
+def test_plane_waves_rank_sum():
+    w = inputs.plane_waves((6, 8, 10), 5, n_waves=16)
+    wa, wk, wphi = inputs._wave_params((6, 8, 10), 5, 16)
+    z, y, x = 2, 3, 7
+    direct = sum(a * math.cos(2 * math.pi * (k[0] * x / 10 + k[1] * y / 8 + k[2] * z / 6) + p)
+                 for a, k, p in zip(wa, wk, wphi))
+    assert math.isclose(w[z, y, x], direct, rel_tol=1e-12, abs_tol=1e-12)

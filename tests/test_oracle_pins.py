@@ -441,3 +441,47 @@ def test_sampled_lines_match_brute_force():
     rows = O.backward_rows(ps.g, nx)
     for i, (y, z) in enumerate(pts):
         assert rel_l2(rows[i], refb[z, y, :]) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(7, 6, 10), (5, 9, 15), (8, 1, 6), (1, 4, 4)])
+def test_sampled_planes_match_brute_force(shape):
+    """forward_kx_planes / backward_z_planes (the whole sampled planes of the
+    full-size checks) against the brute-force 3D sums, the chunks fed in
+    uneven pieces; the inverse on a non-Hermitian input."""
+    nz, ny, nx = shape
+    H = nx // 2 + 1
+    f = rand_real(shape, 31)
+    ref = brute_forward_3d(f)  # [kz][ky][kx]
+    kxs = sorted({0, H - 1, H // 2})
+    chunks = [(z0, f[z0:z0 + 2]) for z0 in range(0, nz, 2)]
+    planes = O.forward_kx_planes(chunks, nx, ny, nz, kxs)  # [k][ky][kz]
+    for i, kx in enumerate(kxs):
+        assert rel_l2(planes[i], ref[:, :, kx].T) < 1e-13
+    F = rand_cplx((nz, ny, H), 32)
+    refb = brute_backward_3d(F, nx)
+    zs = sorted({0, nz - 1, nz // 2})
+    Z = O.to_zyx(F)
+    chunks = [(k0, Z[k0:k0 + 3]) for k0 in range(0, H, 3)]
+    rows = O.backward_z_planes(chunks, nx, ny, nz, zs)
+    for j, z in enumerate(zs):
+        assert rel_l2(rows[j], refb[z]) < 1e-13
+
+
+def test_inverse_z_table_closed_form():
+    T = O.inverse_z_table(4, [0, 1, 3])
+    assert np.allclose(T[:, 0], 1.0, atol=0, rtol=0)
+    assert np.allclose(T[:, 1], [1, 1j, -1, -1j], atol=1e-16)
+    assert np.allclose(T[:, 2], [1, -1j, -1, 1j], atol=1e-16)
+
+
+def test_sampled_plane_checks_catch_a_wrong_sign(monkeypatch):
+    """A planted mistake (the inverse Z table with the forward sign) must make
+    the sampled inverse planes disagree with the brute-force sums."""
+    nz, ny, nx = 6, 5, 8
+    H = nx // 2 + 1
+    F = rand_cplx((nz, ny, H), 33)
+    refb = brute_backward_3d(F, nx)
+    good = O.inverse_z_table
+    monkeypatch.setattr(O.oracle, "inverse_z_table", lambda n, zs, sign=+1: good(n, zs, -sign))
+    rows = O.backward_z_planes([(0, O.to_zyx(F))], nx, ny, nz, [1, 2])
+    assert rel_l2(rows[0], refb[1]) > 1e-3 and rel_l2(rows[1], refb[2]) > 1e-3
