@@ -207,10 +207,24 @@ p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
  * and lets the launch finish.  p3_plan_wait_status() synchronises with the
  * device, returns P3_ERR_TIMEOUT if any wait of this plan gave up since the
  * last check (and clears the mark), else P3_OK; P3_ERR_INVALID for NULL.
- * The waits of the TMA-staged Z kernels (for their tensor copies) report the
- * same way.
+ * The waits of the Z kernels whose input tile arrives by tensor (TMA) or
+ * bulk copies report the same way: a wait that gives up skips that tile
+ * (the output is then invalid) after waiting, again bounded, for the copies
+ * still in flight into the tile.
  */
 p3_status p3_plan_wait_status(p3_plan plan);
+
+/*
+ * As p3_plan_wait_status(), but reports which kinds of wait gave up since
+ * the last check: *flags = 0 when none did, else an OR of
+ * P3_WAIT_FUSED_QUEUE (a plane-fused launch's wait for another tile) and
+ * P3_WAIT_COPY (a Z kernel's wait for its tensor / bulk copies); the marks
+ * are cleared.  Synchronises with the device.  P3_ERR_INVALID for NULL
+ * arguments, P3_ERR_CUDA if the status word cannot be read.
+ */
+#define P3_WAIT_FUSED_QUEUE 1u
+#define P3_WAIT_COPY 2u
+p3_status p3_plan_wait_flags(p3_plan plan, unsigned* flags);
 
 /*
  * Tuning of the plane-fused launches: the consumer tiles of z-plane p are
@@ -223,10 +237,15 @@ p3_status p3_plan_set_fused_lag(p3_plan plan, int lag);
 
 /*
  * Test support for the bounded waits: spin_limit polls (>= 1; default
- * 2^23, over a second) before a wait gives up, and `extra` added to the
- * count of finished tiles a wait needs (0 by default; any extra > 0 makes
- * every wait run out, which is how the tests check the error path).
- * P3_ERR_INVALID for NULL or spin_limit == 0.
+ * 2^23, over a second) before a plane-fused wait gives up (the Z kernels'
+ * copy waits poll spin_limit / 2 times, each poll of the copy barrier may
+ * itself pause briefly), and `extra`, which makes every wait run out
+ * (0 by default): a fused wait then needs `extra` more finished tiles than
+ * exist, and a copy wait one barrier arrival more than the copies make --
+ * after giving up, the kernel makes that arrival itself and waits for its
+ * copies, so the copies into shared memory have landed before it leaves.
+ * This is how the tests check the error path.  P3_ERR_INVALID for NULL or
+ * spin_limit == 0.
  */
 p3_status p3_plan_set_wait_limits(p3_plan plan, unsigned spin_limit, unsigned extra);
 
@@ -313,7 +332,9 @@ p3_status p3_batch_btran_c2r(p3_batch batch, const void* const* in, void* const*
  *     (the transform overwrites every workspace element before reading it,
  *     so nothing needs clearing).  Calls whose kernels overlap on the GPU --
  *     on different streams, or from different threads -- race on it.
- *   - Errors as p3_ftran_r2c, plus P3_ERR_UNSUPPORTED for the size limit.
+ *   - Errors as p3_ftran_r2c, plus P3_ERR_UNSUPPORTED for the size limit
+ *     and for devices numbered 64 or higher (the per-device address table
+ *     has 64 entries).
  */
 #define P3_NOALLOC_SCRATCH_BYTES (64u << 20)
 p3_status p3_ftran_r2c_noalloc(p3_plan plan, const void* in_real, void* out_cplx, void* stream);

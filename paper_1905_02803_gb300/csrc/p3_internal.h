@@ -88,13 +88,6 @@ struct StageArgs {
     size_t smem;       // dynamic shared memory bytes
     int threads;       // B * tpl
     int kern;          // KernelKind
-    // Optional group-major tiling (power-of-two column kernels): lines form
-    // gcount groups of glen adjacent lines (L = g * glen + x); tile i takes
-    // group i % gcount and lines x = (i / gcount) * B + l, so CTAs running
-    // side by side work on different groups.  gcount = 0: tile i takes lines
-    // i * B + l.
-    long long gcount;
-    int glen;
     // 1: tensor-core split-precision kernel (p3_tc.cu)
     int tc;
     // 1: TMA-staged ZYX-store column kernel (input tile by tensor copies);
@@ -102,6 +95,12 @@ struct StageArgs {
     int tma;
     // status word of the plan: a bounded device wait that gave up ORs a bit in
     unsigned* err;
+    // polls before a wait for a tensor / bulk copy gives up
+    unsigned spin;
+    // test mode (1): the copy barrier waits for one arrival more than the
+    // copies make, so the wait runs out; the kernel then supplies the
+    // missing arrival and waits for its copies before it leaves
+    int wait_extra;
 };
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.

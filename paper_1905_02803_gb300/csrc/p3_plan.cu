@@ -28,10 +28,6 @@
 #include "../../include/p3dfft_gb300.h"
 #include "p3_internal.h"
 
-#ifndef P3_Z_GROUP_MAJOR
-#define P3_Z_GROUP_MAJOR 0
-#endif
-
 using p3::LineMap;
 using p3::StageArgs;
 
@@ -586,15 +582,6 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             a.npass = 0;
         }
         tile_setup(a, P->csize, flags);
-        a.gcount = 0;
-        a.glen = 0;
-        if (name[0] == 'z' && a.kern >= p3::KIND_COL_DD && a.kern <= p3::KIND_COL_SD && P3_Z_GROUP_MAJOR) {
-            // Z lines (x, y): CTAs side by side take different y rows, so the
-            // plane-strided accesses of concurrent tiles spread over memory
-            // channels instead of repeating the same plane-pitch offsets.
-            a.gcount = NY;
-            a.glen = (int)H;
-        }
         Stage s;
         s.a = a; s.src = src; s.dst = dst; s.name = name; s.bytes = bytes;
         s.fused = false;
@@ -993,6 +980,8 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
         a.src = bufs[st.src];
         a.dst = bufs[st.dst];
         a.err = P->derr;
+        a.spin = P->spin_limit / 2 > 0 ? P->spin_limit / 2 : 1;
+        a.wait_extra = P->wait_extra ? 1 : 0;
         cudaError_t e;
         if (st.fused) {
             p3::PlaneArgs f = st.f;
@@ -1106,6 +1095,22 @@ p3_status p3_plan_wait_status(p3_plan plan)
         return P3_ERR_CUDA;
     }
     return P3_ERR_TIMEOUT;
+}
+
+p3_status p3_plan_wait_flags(p3_plan plan, unsigned* flags)
+{
+    if (!plan || !flags) return P3_ERR_INVALID;
+    *flags = 0;
+    if (!plan->derr) return P3_OK;
+    if (cudaMemcpy(flags, plan->derr, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return P3_ERR_CUDA;
+    }
+    if (*flags && cudaMemset(plan->derr, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return P3_ERR_CUDA;
+    }
+    return P3_OK;
 }
 
 p3_status p3_plan_set_fused_lag(p3_plan plan, int lag)

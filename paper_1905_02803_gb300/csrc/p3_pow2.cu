@@ -69,14 +69,14 @@ static bool configure(StageArgs& a, size_t csize, bool allow_tma)
     // be adjacent (the tensor's inner dimension) and their elements a
     // 16-byte multiple apart, past the last line
     if (f32 && allow_tma && kind == KIND_COL_DS && N >= 256 && N <= 2048 && a.in.lstride == 1 &&
-        a.in.per >= a.nlines && a.in.es % 2 == 0 && a.in.es >= a.nlines && a.gcount == 0 && (B % 2) == 0) {
+        a.in.per >= a.nlines && a.in.es % 2 == 0 && a.in.es >= a.nlines && (B % 2) == 0) {
         a.tma = 1;
         a.smem = pow2_tma_smem_f32(N, sym_of(a));
     }
     // bulk-copied tile for the row-style ZYX load: plain FFT lines that lie
     // one after another in memory
     if (f32 && allow_tma && kind == KIND_COL_SD && a.op == OP_C2C && a.sign > 0 && a.n_in == N &&
-        a.in.es == 1 && a.in.lstride == N && a.in.per >= a.nlines && a.gcount == 0 && pow2_pick_zbulk_f32(N)) {
+        a.in.es == 1 && a.in.lstride == N && a.in.per >= a.nlines && pow2_pick_zbulk_f32(N)) {
         a.tma = 2;
         a.smem = pow2_zbulk_smem_f32(N);
     }
@@ -120,7 +120,7 @@ cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
                      : (f32 ? pow2_pick_f32(a.kern, a.nfft, inv, sym) : pow2_pick_f64(a.kern, a.nfft, inv, sym));
     if (!fn) return cudaErrorInvalidDeviceFunction;
     if (a.nlines <= 0) return cudaSuccess;
-    long long grid = a.gcount > 0 ? a.gcount * ((a.glen + a.B - 1) / a.B) : (a.nlines + a.B - 1) / a.B;
+    long long grid = (a.nlines + a.B - 1) / a.B;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<StageArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(a.threads), args, a.smem, st);

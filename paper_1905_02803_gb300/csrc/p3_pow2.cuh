@@ -104,15 +104,10 @@ __device__ __forceinline__ long long lbase(const LineMap& m, long long L)
     return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
 }
 
-// Line of lane l of tile `tile` (see StageArgs::gcount); false past the end.
+// Line of lane l of tile `tile` (tile i takes lines i * B + l); false past
+// the end.
 __device__ __forceinline__ bool tile_line(const StageArgs& a, int B, long long tile, int l, long long* L)
 {
-    if (a.gcount > 0) {
-        const long long g = tile % a.gcount;
-        const int x = (int)(tile / a.gcount) * B + l;
-        *L = g * a.glen + x;
-        return x < a.glen;
-    }
     *L = tile * B + l;
     return *L < a.nlines;
 }
@@ -406,8 +401,38 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
     return done != 0;
 }
 
-constexpr unsigned kTmaSpin = 1u << 22;  // try_wait polls before a wait gives up
-constexpr int kTmaRows = 256;            // box height (elements of a line)
+constexpr int kTmaRows = 256;  // box height (elements of a line)
+
+// Copy barrier of a tile: arrival count 1, or 2 in the test mode of
+// StageArgs::wait_extra (one arrival never comes, so the wait runs out).
+__device__ __forceinline__ void copy_bar_init(unsigned bar, int extra)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(extra ? 2 : 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Every thread waits (at most a.spin polls) for the tile's copies; true when
+// all threads saw them land.  Otherwise bit 2 of *a.err is set, the missing
+// test-mode arrival is supplied, and the CTA waits (again bounded) for the
+// copies still in flight into its shared memory before the caller leaves.
+__device__ __forceinline__ bool copy_bar_wait(const StageArgs& a, unsigned bar)
+{
+    int ok = 0;
+    for (unsigned it = 0; it < a.spin; ++it)
+        if (mbar_try_wait(bar, 0)) {
+            ok = 1;
+            break;
+        }
+    if (__syncthreads_and(ok)) return true;
+    if (threadIdx.x == 0) {
+        atomicOr(a.err, 2u);
+        if (a.wait_extra) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+    }
+    __syncthreads();
+    for (unsigned it = 0; it < a.spin && !mbar_try_wait(bar, 0); ++it) {
+    }
+    return false;
+}
 
 template <int N, int SYM> __host__ __device__ constexpr int tma_rows()
 {
@@ -441,10 +466,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
     const unsigned bar = smem_u32(base + AREA);
     const int tid = threadIdx.x, l = tid % B, t = tid / B;
     const long long L0 = (long long)blockIdx.x * B;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
+    if (tid == 0) copy_bar_init(bar, a.wait_extra);
     __syncthreads();
     if (tid == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(TX) : "memory");
@@ -456,18 +478,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                 "l"(reinterpret_cast<unsigned long long>(&a.tmap)), "r"((int)L0), "r"(k * kTmaRows), "r"(bar)
                 : "memory");
     }
-    int ok = 0;
-    for (unsigned it = 0; it < kTmaSpin; ++it)
-        if (mbar_try_wait(bar, 0)) {
-            ok = 1;
-            break;
-        }
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(a.err, 2u);
-        for (unsigned it = 0; it < kTmaSpin && !mbar_try_wait(bar, 0); ++it) {
-        }
-        return;
-    }
+    if (!copy_bar_wait(a, bar)) return;
     const C zero = mk<C>((T)0, (T)0);
     const C* tw = static_cast<const C*>(a.tw);
     C v[E];
@@ -725,10 +736,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
         const unsigned bar = smem_u32(base + zrow_area<T, N, E, B>());
         const long long left = a.nlines - L0;
         const unsigned bytes = (unsigned)((left < B ? left : B) * N * (long long)sizeof(C));
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        }
+        if (tid == 0) copy_bar_init(bar, a.wait_extra);
         __syncthreads();
         if (tid == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
@@ -737,18 +745,7 @@ __global__ void __launch_bounds__(B * (N / E), (MinBlocks<B * (N / E), 2 * sizeo
                          "l"(static_cast<const C*>(a.src) + lbase(a.in, L0)), "r"(bytes), "r"(bar)
                          : "memory");
         }
-        int ok = 0;
-        for (unsigned it = 0; it < kTmaSpin; ++it)
-            if (mbar_try_wait(bar, 0)) {
-                ok = 1;
-                break;
-            }
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) atomicOr(a.err, 2u);
-            for (unsigned it = 0; it < kTmaSpin && !mbar_try_wait(bar, 0); ++it) {
-            }
-            return;
-        }
+        if (!copy_bar_wait(a, bar)) return;
 #pragma unroll
         for (int b = 0; b < P0::BM; ++b)
 #pragma unroll

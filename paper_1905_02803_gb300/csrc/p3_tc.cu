@@ -277,7 +277,6 @@ bool tc_configure(StageArgs& a, size_t csize)
     a.tpl = tcs::TPL;
     a.threads = tcs::NT;
     a.smem = (size_t)(pw::cpad_c(tcs::N - 1) + 1) * tcs::B * csize;
-    a.gcount = 0;
     a.tc = 1;
     return true;
 }

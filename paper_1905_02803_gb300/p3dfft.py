@@ -24,11 +24,13 @@ P3_FLAG_PADDED_REAL = 2
 P3_FLAG_NO_FUSE = 4
 P3_FLAG_TUNE = 8
 P3_FLAG_NO_TMA = 16
+P3_WAIT_FUSED_QUEUE, P3_WAIT_COPY = 1, 2
 
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
-           "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_set_wait_limits",
+           "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_wait_flags",
+           "p3_plan_set_wait_limits",
            "p3_plan_set_fused_lag", "p3_batch_create", "p3_batch_destroy", "p3_batch_ftran_r2c",
            "p3_batch_btran_c2r",
            "p3_status_string", "p3_version")
@@ -70,6 +72,7 @@ def load():
     lib.p3_plan_launches.argtypes = [P, I, ctypes.POINTER(I)]
     lib.p3_plan_set_z_hook.argtypes = [P, Z_HOOK, P]
     lib.p3_plan_wait_status.argtypes = [P]
+    lib.p3_plan_wait_flags.argtypes = [P, ctypes.POINTER(U)]
     lib.p3_plan_set_wait_limits.argtypes = [P, U, U]
     lib.p3_plan_set_fused_lag.argtypes = [P, I]
     lib.p3_batch_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(P), I]
@@ -141,9 +144,19 @@ def p3_plan_set_z_hook(plan, hook, user=None, check=True):
 
 
 def p3_plan_wait_status(plan) -> int:
-    """P3_OK, or P3_ERR_TIMEOUT when a bounded wait of a fused launch gave up
-    since the last check (synchronises with the device)."""
+    """P3_OK, or P3_ERR_TIMEOUT when a bounded device wait gave up since the
+    last check (synchronises with the device)."""
     return load().p3_plan_wait_status(plan)
+
+
+def p3_plan_wait_flags(plan, check=True) -> int:
+    """Which kinds of bounded wait gave up since the last check: an OR of
+    P3_WAIT_FUSED_QUEUE and P3_WAIT_COPY, 0 when none (clears the marks)."""
+    f = ctypes.c_uint(0)
+    st = load().p3_plan_wait_flags(plan, ctypes.byref(f))
+    if check:
+        _check(st, "p3_plan_wait_flags")
+    return f.value
 
 
 def p3_plan_set_wait_limits(plan, spin_limit, extra=0, check=True):

@@ -1,4 +1,7 @@
 """Shared helpers for the GPU parity tests (GPU path vs the FP64 oracle)."""
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -17,13 +20,22 @@ def rel_l2(got, ref):
     return d / n if n > 0 else d
 
 
+def log_parity(**kw):
+    """Append one JSON line to the file P3_PARITY_LOG names (if set): the
+    measured errors that the benchmark report quotes."""
+    path = os.environ.get("P3_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(kw) + "\n")
+
+
 def random_complex(shape, seed):
     n = int(np.prod(shape))
     return (inputs.normal(seed, 60, n) + 1j * inputs.normal(seed, 62, n)).reshape(shape)
 
 
 def check_case(nx, ny, nz, prec="f64", ttypes=("fft", "fft", "fft"), layout="zyx", field=None, seed=0,
-               check_inverse=True, flags=0):
+               check_inverse=True, flags=0, label=None):
     """Forward of a real field and inverse of a random (non-Hermitian) complex
     array, each compared element by element with the oracle; returns errors."""
     import torch
@@ -51,4 +63,7 @@ def check_case(nx, ny, nz, prec="f64", ttypes=("fft", "fft", "fft"), layout="zyx
         refb = O.backward(Gin, nx, tt)
         torch.cuda.synchronize()
         err_b = rel_l2(g.cpu().numpy(), refb)
+    if label:
+        log_parity(check="forward+inverse", config=label, grid=[nx, ny, nz], precision=prec, ttypes=list(ttypes),
+                   layout=layout, compared="whole array", rel_l2_forward=err_f, rel_l2_inverse=err_b)
     return err_f, err_b, plan

@@ -115,6 +115,8 @@ def test_null_plan_calls(lib):
     assert P.p3_plan_set_z_hook(None, P.Z_HOOK(lambda *a: 0), check=False) == P.P3_ERR_INVALID
     assert P.p3_status_string(P.P3_ERR_HOOK) == "user Z hook failed"
     assert P.p3_plan_wait_status(None) == P.P3_ERR_INVALID
+    f = ctypes.c_uint(7)
+    assert lib.p3_plan_wait_flags(None, ctypes.byref(f)) == P.P3_ERR_INVALID
     assert P.p3_plan_set_wait_limits(None, 10, 0, check=False) == P.P3_ERR_INVALID
     assert P.p3_plan_set_fused_lag(None, 1, check=False) == P.P3_ERR_INVALID
     st, h = P.p3_batch_create(None, 2, check=False)

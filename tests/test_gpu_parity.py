@@ -20,8 +20,8 @@ pytestmark = pytest.mark.gpu
 def test_config1_32cubed_fp64_plane_wave(layout):
     """32^3 FP64: U[-1,1) field plus sin(2 pi 3 x/32), and the plane wave alone."""
     total, rnd, wave = inputs.config1_field(32, seed=0)
-    for field in (total, wave, rnd):
-        ef, eb, _ = check_case(32, 32, 32, "f64", layout=layout, field=field)
+    for field, name in ((total, "32cube_f64 U[-1,1)+sin"), (wave, "32cube_f64 sin"), (rnd, "32cube_f64 U[-1,1)")):
+        ef, eb, _ = check_case(32, 32, 32, "f64", layout=layout, field=field, label=name)
         assert ef <= TOL["f64"] and eb <= TOL["f64"], (ef, eb)
 
 
@@ -78,7 +78,8 @@ def test_config4_channel_480x360x257_fp64():
     """Uneven channel-flow grid: FFT in X and Y, Chebyshev (DCT-I) in Z."""
     nx, ny, nz = 480, 360, 257
     f = inputs.channel_field(nx, ny, nz, seed=0)
-    ef, eb, _ = check_case(nx, ny, nz, "f64", ttypes=("fft", "fft", "cheb"), layout="zyx", field=f)
+    ef, eb, _ = check_case(nx, ny, nz, "f64", ttypes=("fft", "fft", "cheb"), layout="zyx", field=f,
+                           label="channel_480x360x257_f64")
     assert ef <= TOL["f64"] and eb <= TOL["f64"], (ef, eb)
 
 

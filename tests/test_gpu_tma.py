@@ -56,3 +56,49 @@ def test_bulk_zyx_load_matches(shape):
     torch.cuda.synchronize()
     assert torch.equal(yt, yn)
     assert P.p3_plan_wait_status(pt.handle) == P.P3_OK
+
+
+def test_tma_copy_wait_gives_up_and_reports():
+    """The forward Z stage's wait for its tensor copies: with the test knob
+    the barrier needs one arrival more than the copies make, so every wait
+    runs out; the plan reports a copy wait (and no other kind), the launch
+    finishes, and with the default limits the next call is exact again."""
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = 64, 32, 1024
+    pt = P.Plan(nx, ny, nz, precision="f32", layout="zyx", flags=P.P3_FLAG_NO_FUSE)
+    pn = P.Plan(nx, ny, nz, precision="f32", layout="zyx", flags=P.P3_FLAG_NO_FUSE | P.P3_FLAG_NO_TMA)
+    assert "zyx_store_tma" in pt.describe(), pt.describe()
+    x = torch.from_numpy(inputs.uniform_field((nz, ny, nx), 11)).to("cuda", torch.float32)
+    P.p3_plan_set_wait_limits(pt.handle, 2000, 1)
+    pt.forward(x)
+    torch.cuda.synchronize()
+    assert P.p3_plan_wait_flags(pt.handle) == P.P3_WAIT_COPY
+    assert P.p3_plan_wait_status(pt.handle) == P.P3_OK  # the mark was cleared
+    P.p3_plan_set_wait_limits(pt.handle, 1 << 23, 0)
+    Xt, Xn = pt.forward(x), pn.forward(x)
+    torch.cuda.synchronize()
+    assert P.p3_plan_wait_status(pt.handle) == P.P3_OK
+    assert torch.equal(Xt, Xn)
+
+
+def test_bulk_copy_wait_gives_up_and_reports():
+    """The inverse Z stage's wait for its bulk-copied tile, the same way (the
+    plan's plane-fused launch gives up too under the knob)."""
+    import torch
+    from paper_1905_02803_gb300 import p3dfft as P
+    nx, ny, nz = 512, 256, 256
+    pt = P.Plan(nx, ny, nz, precision="f32", layout="zyx")
+    pn = P.Plan(nx, ny, nz, precision="f32", layout="zyx", flags=P.P3_FLAG_NO_TMA)
+    assert "pow2_zrow_bulk" in pt.describe(), pt.describe()
+    G = torch.from_numpy(np.asarray(inputs.normal(6, 1, 2 * (nx // 2 + 1) * ny * nz), dtype=np.float32)).cuda()
+    X = torch.view_as_complex(G.view(nx // 2 + 1, ny, nz, 2))
+    P.p3_plan_set_wait_limits(pt.handle, 2000, 1)
+    pt.backward(X)
+    torch.cuda.synchronize()
+    assert P.p3_plan_wait_flags(pt.handle) & P.P3_WAIT_COPY
+    P.p3_plan_set_wait_limits(pt.handle, 1 << 23, 0)
+    yt, yn = pt.backward(X), pn.backward(X)
+    torch.cuda.synchronize()
+    assert P.p3_plan_wait_flags(pt.handle) == 0
+    assert torch.equal(yt, yn)

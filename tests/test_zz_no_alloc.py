@@ -17,8 +17,11 @@ from _gpu_helpers import TOL, rel_l2
 pytestmark = pytest.mark.gpu
 
 
+# (512, 256, 64) FP32 runs the plane-fused X+Y launch: its queue counters
+# (cleared by the call itself) and its transposed [x][y] planes, which the Z
+# stage reads, both live in the built-in array
 @pytest.mark.parametrize("shape,prec", [((64, 48, 40), "f32"), ((128, 96, 64), "f64"), ((30, 20, 12), "f32"),
-                                        ((256, 128, 96), "f32")])
+                                        ((256, 128, 96), "f32"), ((512, 256, 64), "f32")])
 def test_noalloc_matches_workspace_entry_point(shape, prec):
     import torch
     from paper_1905_02803_gb300 import p3dfft as P
@@ -26,6 +29,9 @@ def test_noalloc_matches_workspace_entry_point(shape, prec):
     nx, ny, nz = shape
     plan = P.Plan(nx, ny, nz, precision=prec, layout="zyx")
     assert 0 < plan.ws_bytes <= P.P3_NOALLOC_SCRATCH_BYTES
+    if shape == (512, 256, 64):
+        d = plan.describe()
+        assert "plane_fused" in d, d
     x = torch.from_numpy(inputs.uniform_field((nz, ny, nx), seed=nx)).to("cuda", plan.real_dtype)
     ref = plan.forward(x).cpu().numpy()  # caller-supplied workspace
     stream = torch.cuda.current_stream().cuda_stream
