@@ -41,6 +41,54 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def fp64_peak_tflops(n=4096, reps=5):
+    """Measured FP64 arithmetic peak of this GPU: cuBLAS DGEMM (torch.matmul
+    on float64 n x n matrices, 2 n^3 flop), best of `reps`, CUDA events.  The
+    FP64 transforms are compared with it (their FP64 operations per launch
+    come from ncu, profiles/fp64_ops.json)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b, out=c)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def fp64_ops_record(config):
+    """FP64 work of one forward + inverse pair of a report configuration
+    (ncu counters, profiles/fp64_ops.json): (flop, FP64-pipe instructions),
+    a DFMA counting 2 flop and each of DFMA, DADD, DMUL one instruction.
+    None when absent or when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for rel in rec.get("kernel_sources", []):
+        try:
+            h.update(open(os.path.join(ROOT, rel), "rb").read())
+        except OSError:
+            return None
+    if not rec.get("kernel_sources") or rec.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+        return None
+    ent = rec.get("configs", {}).get(config)
+    return None if ent is None else (float(ent["fp64_flop_per_pair"]), float(ent["fp64_inst_per_pair"]))
+
+
 def stage_model_bytes(nx, ny, nz, e):
     """Algorithmic bytes of each stage launch (each stage reads and writes its
     whole array once): X stages e*N + 2e*H*Ny*Nz, Y and Z stages 2 * 2e*H*Ny*Nz."""
@@ -618,13 +666,35 @@ def _report_one(name, dims, prec, ttypes, layout, kind, mode="", *, steps, warmu
         num += (torch.linalg.vector_norm(y[z0:z0 + 64].double() / plan.scale - xd) ** 2).item()
         den += (torch.linalg.vector_norm(xd) ** 2).item()
     rt = math.sqrt(num / den)
-    return {"config": name, "grid": list(dims), "precision": prec, "ttypes": list(ttypes), "layout": layout,
-            "in_place": inplace,
-            "ms": round(ms, 4), "gflops": round(gflops, 1), "stage_model_bytes": pair_bytes,
-            "hbm_roofline_ms": round(roof_ms, 4), "hbm_roofline_frac": round(roof_ms / ms, 4),
-            "round_trip_rel_l2": rt,
-            "parity": "oracle comparison in tests/test_gpu_fullsize.py and tests/test_gpu_parity.py "
-                      "(P3_PARITY_LOG records the measured errors)"}
+    out = {"config": name, "grid": list(dims), "precision": prec, "ttypes": list(ttypes), "layout": layout,
+           "in_place": inplace,
+           "ms": round(ms, 4), "gflops": round(gflops, 1), "stage_model_bytes": pair_bytes,
+           "hbm_roofline_ms": round(roof_ms, 4), "hbm_roofline_frac": round(roof_ms / ms, 4)}
+    if prec == "f64":
+        # the FP64 transforms are bound by the FP64 pipe: their roofline is
+        # max(HBM time, FP64-pipe instructions / measured FP64 issue rate),
+        # the rate being the DGEMM peak over 2 flop per DFMA (a DADD or DMUL
+        # takes the pipe for the same slot as a DFMA)
+        ops = fp64_ops_record(name)
+        pk = fp64_peak_tflops()
+        out["fp64_peak_tflops"] = round(pk, 3)
+        out["fp64_peak_kind"] = "measured (cuBLAS DGEMM, torch.matmul float64 4096^3, best of 5)"
+        if ops is not None:
+            flop, inst = ops
+            alu_ms = inst / (pk * 1e12 / 2.0) * 1e3
+            out["fp64_flop_per_pair"] = flop
+            out["fp64_inst_per_pair"] = inst
+            out["fp64_flop_frac"] = round(flop / (pk * 1e12) * 1e3 / ms, 4)
+            out["fp64_alu_ms"] = round(alu_ms, 4)
+            out["fp64_alu_frac"] = round(alu_ms / ms, 4)
+            out["roofline_bound"] = "fp64" if alu_ms > roof_ms else "hbm"
+            out["roofline_frac"] = round(max(alu_ms, roof_ms) / ms, 4)
+        else:
+            out["fp64_alu_frac"] = None
+    out.update({"round_trip_rel_l2": rt,
+                "parity": "oracle comparison in tests/test_gpu_fullsize.py and tests/test_gpu_parity.py "
+                          "(P3_PARITY_LOG records the measured errors)"})
+    return out
 
 
 def _report_batch(steps, warmup, nstreams=16):
@@ -683,19 +753,30 @@ def _report_batch(steps, warmup, nstreams=16):
         torch.cuda.synchronize()
         return timed(g.replay)
 
+    pbatch = P.Batch(plans, nstreams=0)
+
+    def persistent():
+        pbatch.forward(xs, Xs)
+        pbatch.backward(Xs, ys)
+
     ms = timed(serial)
     ms_graph = graphed(serial)
     ms_batch = timed(batched)
     ms_batch_graph = graphed(batched)
+    ms_pers = timed(persistent)
+    ms_pers_graph = graphed(persistent)
     pair_bytes = sum(sum(stage_model_bytes(nx, ny, nz, 4)) for nx, ny, nz in dims)
     peak, _ = peaks()
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
-    best = min(ms, ms_graph, ms_batch, ms_batch_graph)
+    best = min(ms, ms_graph, ms_batch, ms_batch_graph, ms_pers, ms_pers_graph)
     launches = sum(p.launches(0) + p.launches(1) for p in plans)
+    pers_launches = pbatch.launches(0) + pbatch.launches(1)
     kinds = sorted({l.split()[2] for p in plans for l in p.describe().splitlines() if "kernel=" in l})
     return {"config": "batch64_smooth7_f32", "grids": len(dims), "ms": round(best, 4),
             "ms_serial": round(ms, 4), "ms_serial_cuda_graph": round(ms_graph, 4),
             "ms_batch_streams": round(ms_batch, 4), "ms_batch_streams_cuda_graph": round(ms_batch_graph, 4),
+            "ms_persistent": round(ms_pers, 4), "ms_persistent_cuda_graph": round(ms_pers_graph, 4),
+            "persistent_launches_per_step": pers_launches,
             "batch_streams": nstreams, "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
             "hbm_roofline_frac": round(roof_ms / best, 4), "launches_per_step": launches, "kernels": kinds}
 

@@ -285,15 +285,29 @@ p3_status p3_plan_set_z_hook(p3_plan plan, p3_z_hook fn, void* user);
 
 /*
  * Batched execution of independent plans (no paper counterpart: many 3D
- * transforms per call).  A batch spreads its plans over `nstreams` internal
- * streams (largest plans first, each to the least loaded stream), so the
- * launches of different plans overlap on the GPU.
+ * transforms per call), in one of two modes.
+ *   Persistent (nstreams == 0): one kernel launch per call runs every stage
+ *     of every plan.  Each stage is a task of the generic stage kernel; the
+ *     launch's CTAs take (task, tile) tickets level by level (every plan's
+ *     first stage, then every plan's second, ...), and a tile of a later
+ *     stage waits, bounded, until the plan's previous stage has finished
+ *     (see p3_batch_wait_status).  FP32 plans without a Z hook, at most 256
+ *     plans.  The call's buffers are launch parameters, so consecutive calls
+ *     never share host state, and the call can be captured into a CUDA
+ *     graph.  Results equal each plan's own within rounding (the power-of-two
+ *     and plane-fused kernels a plan may use alone are not used here).
+ *   Streams (nstreams >= 1): the plans' own launches spread over nstreams
+ *     internal streams (largest plans first, each to the least loaded
+ *     stream), so the launches of different plans overlap on the GPU;
+ *     results equal each plan's own bit for bit.
  *
  * p3_batch_create: plans (nplans >= 1, all created on the current device;
  *   the batch keeps the handles, not copies: destroy the batch first),
- *   nstreams >= 1 (capped at nplans).  Creates the streams and events.
- *   P3_ERR_INVALID on bad arguments, P3_ERR_CUDA if a stream or event
- *   cannot be created.
+ *   nstreams >= 0 (capped at nplans).  Creates the streams and events, or
+ *   the persistent mode's task tables (device memory owned by the batch).
+ *   P3_ERR_INVALID on bad arguments, P3_ERR_UNSUPPORTED when the persistent
+ *   mode cannot take a plan (FP64, a Z hook, more than 256 plans),
+ *   P3_ERR_NOMEM / P3_ERR_CUDA if the batch's resources cannot be created.
  * p3_batch_ftran_r2c / p3_batch_btran_c2r: arrays of nplans pointers in
  *   plan order: in[i], out[i], ws[i] as p3_ftran_r2c / p3_btran_c2r take
  *   them for plan i (ws may be NULL when no plan needs a workspace, and
@@ -311,6 +325,26 @@ p3_status p3_batch_ftran_r2c(p3_batch batch, const void* const* in, void* const*
                              void* stream);
 p3_status p3_batch_btran_c2r(p3_batch batch, const void* const* in, void* const* out, void* const* ws,
                              void* stream);
+
+/* Persistent mode: P3_ERR_TIMEOUT if a tile's bounded wait for the previous
+   stage of its plan gave up since the last check (that call's outputs are
+   invalid; the mark is cleared), else P3_OK.  Synchronises with the device.
+   Stream mode: P3_OK (each plan reports through p3_plan_wait_status).
+   P3_ERR_INVALID for NULL. */
+p3_status p3_batch_wait_status(p3_batch batch);
+
+/* Persistent mode, as p3_plan_set_wait_limits: spin_limit polls before a
+   tile's wait gives up (default 2^23, over a second), and `extra` finished
+   tiles more than exist needed by every wait (0 by default; > 0 makes every
+   wait run out, for tests of the error path).  P3_ERR_INVALID for NULL or
+   spin_limit == 0. */
+p3_status p3_batch_set_wait_limits(p3_batch batch, unsigned spin_limit, unsigned extra);
+
+/* Kernel launches one batch call makes in direction dir (0 forward, 1
+   inverse): 1 in persistent mode, the plans' launches summed in stream
+   mode (counter memsets are not launches).  P3_ERR_INVALID on bad
+   arguments. */
+p3_status p3_batch_launches(p3_batch batch, int dir, int* launches);
 
 /*
  * p3_ftran_r2c_noalloc -- the forward transform of p3_ftran_r2c, but with the

@@ -288,7 +288,27 @@ __global__ void __launch_bounds__(NT, (TP ? (DIR == 0 ? P3_FUSED_MINB_TP_FWD : P
             r = v % second;
             prod = false;
         }
-        if (!prod) {
+        // Consumer tiles whose lines each belong to one warp (forward Y tiles
+        // of transposed planes, lines of at most 32 lanes) wait warp by warp
+        // and need no block barrier; other consumers wait as a block.
+        constexpr bool WARP_Y = TP && DIR == 0 && (NY / EY) <= 32;
+        if (!prod && WARP_Y) {
+            int ok = 1;
+            if ((threadIdx.x & 31) == 0) {
+                const unsigned* done = f.ctr + 1 + plane;
+                const unsigned need = first + f.extra;
+                unsigned it = 0;
+                while (ld_acquire(done) < need) {
+                    if (++it > f.spin_limit || ld_acquire(f.err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+                if (!ok) atomicOr(f.err, 1u);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) continue;  // the output is invalid; the host reads *err
+        } else if (!prod) {
             if (threadIdx.x == 0) {
                 const unsigned* done = f.ctr + 1 + plane;
                 const unsigned need = first + f.extra;
@@ -340,10 +360,15 @@ __global__ void __launch_bounds__(NT, (TP ? (DIR == 0 ? P3_FUSED_MINB_TP_FWD : P
             else
                 col_tile<T, NY, EY, BY, 0, true, 0, LD_DEF, ST_DEF>(f.y, r, (long long)plane * f.yoff, s);
         }
-        __syncthreads();
-        if (prod && threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(f.ctr + 1 + plane, 1u);
+        // a producer counts its tile once every thread's stores are issued;
+        // consumers go straight on (the barrier at the top of the loop keeps
+        // the next tile from reusing shared memory too early)
+        if (prod) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(f.ctr + 1 + plane, 1u);
+            }
         }
     }
 }

@@ -154,6 +154,44 @@ cudaError_t fused_prepare();
 cudaError_t fused_launch(const PlaneArgs& f, cudaStream_t s);
 
 
+// A stage of a plan configured for the generic kernel, with its buffer
+// roles (0 input, 1 output, 2 workspace): the building block of the batched
+// persistent launch.
+struct GenericStage {
+    StageArgs a;
+    int src, dst;
+};
+
+// Batched persistent launch (p3_batch.cu builds the task table, the kernel
+// is in p3_kernels.cu).  Every (plan, stage) of a direction is a task of
+// ntiles tiles; task i owns tickets first .. first + ntiles - 1; tasks are
+// ordered level by level (every plan's first stage, then every plan's
+// second, ...), so a tile only waits for tiles of a lower level, which
+// running CTAs already hold.
+struct BatchTask {
+    StageArgs a;        // generic-kernel stage; src and dst come from the call
+    long long first;    // first ticket
+    long long ntiles;
+    int plan;           // row of the call's buffer table
+    int src, dst;       // buffer roles
+    int dep;            // task that must be finished first, or -1
+};
+constexpr int kBatchMaxPlans = 256;
+struct BatchLaunch {
+    const BatchTask* tasks;  // device array, ntasks entries
+    int ntasks;
+    unsigned total;          // tickets
+    unsigned* ctr;           // [0] next ticket, [1 + i] finished tiles of task i (zeroed before the launch)
+    unsigned* err;           // set non-zero when a wait gives up
+    unsigned spin_limit;     // polls before a wait gives up
+    unsigned extra;          // added to the count a wait needs (0; > 0 only in tests)
+    void* buf[kBatchMaxPlans][3];
+};
+// Resident CTAs of the batched kernel for `smem` bytes of dynamic shared
+// memory (sets the kernel's shared-memory limit); 0 on failure.
+int batch_grid(size_t smem);
+cudaError_t batch_launch(const BatchLaunch& b, int grid, size_t smem, cudaStream_t s);
+
 // Tensor-core split-precision kernels (p3_tc.cu): FP32 1024-point columns.
 bool tc_configure(StageArgs& a, size_t csize);
 cudaError_t tc_prepare();

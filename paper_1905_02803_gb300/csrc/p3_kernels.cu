@@ -270,15 +270,17 @@ __device__ __forceinline__ void store_value(const StageArgs& a, const C* sl, int
 #ifndef P3_GEN_MINB_F64
 #define P3_GEN_MINB_F64 2
 #endif
+// One tile (lines tile * B .. tile * B + B - 1) of a generic stage, by all
+// blockDim.x threads of the CTA (at least a.threads); smem_raw holds a.smem
+// bytes.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P3_GEN_MINB_F64)) stage_kernel(const __grid_constant__ StageArgs a)
+__device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, unsigned char* smem_raw)
 {
     typedef typename Cx<T>::t C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int B = a.B, LDB = a.LDB;
-    const long long L0 = (long long)blockIdx.x * B;
+    const long long L0 = tile * B;
     const int nload = a.blue ? a.m : a.nfft;  // slots filled per line
     const int nfill = a.blue ? a.nfft : nload;  // slots taken from the input
     C* s0 = reinterpret_cast<C*>(smem_raw);
@@ -440,6 +442,14 @@ __global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P3_GEN_MINB_F64))
+    stage_kernel(const __grid_constant__ StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<T>(a, blockIdx.x, smem_raw);
+}
+
+template <typename T>
 cudaError_t launch_stage(const StageArgs& a, cudaStream_t st)
 {
     if (a.nlines <= 0) return cudaSuccess;
@@ -449,7 +459,106 @@ cudaError_t launch_stage(const StageArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Batched persistent launch: every CTA takes tickets in order; a ticket is a
+// tile of one (plan, stage) task; the task's arguments are copied to shared
+// memory and the call's buffers filled in; a tile of a later stage first
+// waits (bounded) until every tile of the plan's previous stage finished.
+// A wait that gives up marks *err and skips the tile (the output of that
+// call is invalid), still counting it as finished so no wait behind it hangs.
+#ifndef P3_BATCH_MINB
+#define P3_BATCH_MINB P3_GEN_MINB
+#endif
+__global__ void __launch_bounds__(kMaxThreads, P3_BATCH_MINB) batch_kernel(const __grid_constant__ BatchLaunch b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ StageArgs sa;
+    __shared__ long long s_tile;
+    __shared__ int s_task, s_ok;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned tk = atomicAdd(b.ctr, 1u);
+            int task = -1;
+            if (tk < b.total) {
+                int lo = 0, hi = b.ntasks - 1;  // last task with first <= tk
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (b.tasks[mid].first <= (long long)tk) lo = mid;
+                    else hi = mid - 1;
+                }
+                task = lo;
+                s_tile = (long long)tk - b.tasks[lo].first;
+            }
+            s_task = task;
+        }
+        __syncthreads();
+        const int task = s_task;
+        if (task < 0) return;
+        {
+            const int* srcw = reinterpret_cast<const int*>(&b.tasks[task].a);
+            int* dstw = reinterpret_cast<int*>(&sa);
+            for (int i = tid; i < (int)(sizeof(StageArgs) / sizeof(int)); i += blockDim.x) dstw[i] = srcw[i];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const BatchTask& t = b.tasks[task];
+            sa.src = b.buf[t.plan][t.src];
+            sa.dst = b.buf[t.plan][t.dst];
+            int ok = 1;
+            if (t.dep >= 0) {
+                const unsigned need = (unsigned)b.tasks[t.dep].ntiles + b.extra;
+                unsigned it = 0;
+                while (ld_acquire_u32(b.ctr + 1 + t.dep) < need) {
+                    if (++it > b.spin_limit || ld_acquire_u32(b.err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+                if (!ok) atomicOr(b.err, 1u);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) stage_tile<float>(sa, s_tile, smem_raw);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(b.ctr + 1 + task, 1u);
+        }
+    }
+}
+
 }  // namespace
+
+int batch_grid(size_t smem)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kMaxThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+cudaError_t batch_launch(const BatchLaunch& b, int grid, size_t smem, cudaStream_t s)
+{
+    if (b.total == 0) return cudaSuccess;
+    const cudaError_t e = cudaMemsetAsync(b.ctr, 0, sizeof(unsigned) * (size_t)(1 + b.ntasks), s);
+    if (e != cudaSuccess) return e;
+    batch_kernel<<<grid, kMaxThreads, smem, s>>>(b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stage_f32(const StageArgs& a, cudaStream_t s)
 {

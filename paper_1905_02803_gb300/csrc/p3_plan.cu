@@ -68,6 +68,9 @@ struct p3_plan_s {
     // st[0] forward, st[1] inverse, st[2] the inverse used while a Z hook is
     // set (EMPTY third dimension: a Z copy into the work buffer comes first)
     std::vector<Stage> st[3];
+    // the stage lists before plane fusion, with their tables (the generic
+    // stages of the batched persistent launch start from these)
+    std::vector<Stage> st_unfused[2];
     p3_z_hook hook;
     void* hook_user;
     size_t ctr_off;     // byte offset of the fused kernels' counters in the workspace
@@ -297,11 +300,12 @@ p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
 }
 
 // Lines per CTA, pitch, threads and shared memory of a stage.
-void tile_setup(StageArgs& a, size_t csize, unsigned flags)
+// Tile shape of the generic kernel: B lines per CTA (a power of two) so that
+// the ping-pong buffers fit 100 KB, LDB the shared-memory pitch.
+void generic_tile_setup(StageArgs& a, size_t csize, size_t cap = 100 * 1024)
 {
     const int len = a.blue ? a.m : (a.nfft > 0 ? a.nfft : 1);
     const bool elem = a.in_elem_fast || a.out_elem_fast;
-    const size_t cap = 100 * 1024;
     int B = pow2_floor(p3::kMaxThreads / a.tpl);
     if (B < 1) B = 1;
     while (B > 1 && 2 * (size_t)len * (size_t)(B + 1) * csize > cap) B /= 2;
@@ -315,6 +319,12 @@ void tile_setup(StageArgs& a, size_t csize, unsigned flags)
     a.smem = 2 * (size_t)len * (size_t)a.LDB * csize;  // ping-pong buffers
     a.kern = p3::KIND_GENERIC;
     a.tc = 0;
+    a.tma = 0;
+}
+
+void tile_setup(StageArgs& a, size_t csize, unsigned flags)
+{
+    generic_tile_setup(a, csize);
     p3::pow2_configure(a, csize, !(flags & P3_FLAG_NO_TMA));
     if (flags & P3_FLAG_TC_SPLIT) p3::tc_configure(a, csize);
 }
@@ -838,6 +848,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             return P3_ERR_NOMEM;
         }
     }
+    P->st_unfused[0] = unfused[0];
+    P->st_unfused[1] = unfused[1];
     // ---- autotuning (P3_FLAG_TUNE) -------------------------------------------
     std::string tuned;
     if ((flags & P3_FLAG_TUNE) && any_fused) {
@@ -941,7 +953,11 @@ static int call_hook(p3_plan P, int dir, void* data, void* stream)
     return P->hook(data, P->nz, H * NY, zyx ? NZ : 1, zyx ? 1 : H * NY, dir, stream, P->hook_user);
 }
 
-static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, void* stream)
+// The argument checks of a call (Sect. 3.2 semantics: const input, caller
+// buffers), without launching: NULL / misaligned / overlapping buffers, a
+// missing workspace, the wrong device.  uses_ws: whether `stages` use it.
+static p3_status check_call(p3_plan P, int dir, const void* in, void* out, void* ws,
+                            const std::vector<Stage>& stages)
 {
     if (!P || !in || !out) return P3_ERR_INVALID;
     if (!aligned16(in) || !aligned16(out) || (ws && !aligned16(ws))) return P3_ERR_INVALID;
@@ -951,12 +967,6 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
     const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
     const size_t nin = dir == 0 ? nreal : ncplx, nout = dir == 0 ? ncplx : nreal;
     if (in != out && overlap(in, nin, out, nout)) return P3_ERR_INVALID;
-    // a Z hook replaces the empty third-dimension transform: forward, it
-    // runs after the last stage; inverse, after the copy of the input into
-    // the work buffer that starts the hook-mode stage list
-    const p3_z_hook hook = P->hook;
-    const std::vector<Stage>& stages = (dir == 1 && hook) ? P->st[2] : P->st[dir];
-    const size_t hook_after = hook ? (dir == 0 ? stages.size() : 1) : 0;
     bool uses_ws = false;
     for (auto& s : stages)
         if (s.src == BUF_WS || s.dst == BUF_WS || s.fused) uses_ws = true;
@@ -970,6 +980,20 @@ static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, vo
         return P3_ERR_CUDA;
     }
     if (cur != P->device) return P3_ERR_INVALID;
+    return P3_OK;
+}
+
+static p3_status run(p3_plan P, int dir, const void* in, void* out, void* ws, void* stream)
+{
+    if (!P || !in || !out) return P3_ERR_INVALID;
+    // a Z hook replaces the empty third-dimension transform: forward, it
+    // runs after the last stage; inverse, after the copy of the input into
+    // the work buffer that starts the hook-mode stage list
+    const p3_z_hook hook = P->hook;
+    const std::vector<Stage>& stages = (dir == 1 && hook) ? P->st[2] : P->st[dir];
+    const size_t hook_after = hook ? (dir == 0 ? stages.size() : 1) : 0;
+    const p3_status chk = check_call(P, dir, in, out, ws, stages);
+    if (chk != P3_OK) return chk;
     cudaStream_t s = (cudaStream_t)stream;
     void* const bufs[3] = {const_cast<void*>(in), out, ws};
     cudaEvent_t* ev = P->timing ? (cudaEvent_t*)&P->events[dir * 4] : NULL;
@@ -1141,11 +1165,47 @@ p3_status p3_plan_set_z_hook(p3_plan plan, p3_z_hook fn, void* user)
 
 }  // extern "C"
 
+#ifndef P3_BATCH_SMEM
+#define P3_BATCH_SMEM (54 * 1024)
+#endif
+
 namespace p3 {
 p3_status run_direction(p3_plan plan, int dir, const void* in, void* out, void* ws, void* stream)
 {
     return run(plan, dir, in, out, ws, stream);
 }
+p3_status generic_stages(p3_plan P, int dir, std::vector<GenericStage>& out)
+{
+    out.clear();
+    if (!P || (dir != 0 && dir != 1)) return P3_ERR_INVALID;
+    for (const Stage& s : P->st_unfused[dir]) {
+        GenericStage g;
+        g.a = s.a;
+        if (g.a.op != OP_COPY) {
+            const int len = g.a.blue ? g.a.m : g.a.nfft;
+            if (len > 1) {
+                const int* r = g.a.blue ? g.a.mrad : g.a.rad;
+                const int np = g.a.blue ? g.a.mpass : g.a.npass;
+                g.a.tpl = threads_per_line(len, std::vector<int>(r, r + np));
+            } else {
+                g.a.tpl = 1;
+            }
+        }
+        // tiles of at most P3_BATCH_SMEM bytes, so that the batched kernel
+        // keeps its resident CTAs whatever stage it runs
+        generic_tile_setup(g.a, P->csize, P3_BATCH_SMEM);
+        g.src = s.src;
+        g.dst = s.dst;
+        out.push_back(g);
+    }
+    return P3_OK;
+}
+p3_status check_generic_call(p3_plan P, int dir, const void* in, void* out, void* ws)
+{
+    if (!P || (dir != 0 && dir != 1)) return P3_ERR_INVALID;
+    return check_call(P, dir, in, out, ws, P->st_unfused[dir]);
+}
+bool plan_batchable(p3_plan P) { return P && P->prec == P3_F32 && !P->hook; }
 size_t plan_workspace(p3_plan plan) { return plan ? plan->ws_bytes : 0; }
 double plan_work(p3_plan plan) { return plan ? (double)plan->nx * plan->ny * plan->nz : 0.0; }
 int plan_device(p3_plan plan) { return plan ? plan->device : -1; }

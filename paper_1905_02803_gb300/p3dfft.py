@@ -32,7 +32,7 @@ EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", 
            "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_wait_flags",
            "p3_plan_set_wait_limits",
            "p3_plan_set_fused_lag", "p3_batch_create", "p3_batch_destroy", "p3_batch_ftran_r2c",
-           "p3_batch_btran_c2r",
+           "p3_batch_btran_c2r", "p3_batch_wait_status", "p3_batch_set_wait_limits", "p3_batch_launches",
            "p3_status_string", "p3_version")
 
 # int hook(void* data, int n, long long nlines, long long line_stride, long long elem_stride,
@@ -79,6 +79,9 @@ def load():
     lib.p3_batch_destroy.argtypes = [P]
     lib.p3_batch_ftran_r2c.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.p3_batch_btran_c2r.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
+    lib.p3_batch_wait_status.argtypes = [P]
+    lib.p3_batch_set_wait_limits.argtypes = [P, U, U]
+    lib.p3_batch_launches.argtypes = [P, I, ctypes.POINTER(I)]
     lib.p3_status_string.argtypes = [I]
     lib.p3_status_string.restype = ctypes.c_char_p
     lib.p3_version.argtypes = []
@@ -205,6 +208,25 @@ def p3_batch_btran_c2r(batch, ins, outs, wss, stream, check=True):
     if check:
         _check(st, "p3_batch_btran_c2r")
     return st
+
+
+def p3_batch_wait_status(batch) -> int:
+    """P3_OK, or P3_ERR_TIMEOUT when a persistent batch's bounded wait gave
+    up since the last check (synchronises with the device)."""
+    return load().p3_batch_wait_status(batch)
+
+
+def p3_batch_set_wait_limits(batch, spin_limit, extra=0, check=True):
+    st = load().p3_batch_set_wait_limits(batch, int(spin_limit), int(extra))
+    if check:
+        _check(st, "p3_batch_set_wait_limits")
+    return st
+
+
+def p3_batch_launches(batch, direction: int) -> int:
+    v = ctypes.c_int()
+    _check(load().p3_batch_launches(batch, int(direction), ctypes.byref(v)), "p3_batch_launches")
+    return v.value
 
 
 def p3_ftran_r2c_noalloc(plan, in_ptr, out_ptr, stream, check=True):
@@ -400,13 +422,19 @@ class Plan:
 
 
 class Batch:
-    """Independent plans run side by side on `nstreams` internal streams
-    (p3_batch_*): forward(xs) / backward(Xs) take one tensor per plan."""
+    """Independent plans in one batch (p3_batch_*): nstreams = 0 runs every
+    call as one persistent launch, nstreams >= 1 spreads the plans' own
+    launches over that many internal streams.  forward(xs) / backward(Xs)
+    take one tensor per plan."""
 
     def __init__(self, plans, nstreams=8):
         self.plans = list(plans)
         self.torch = self.plans[0].torch
+        self.nstreams = int(nstreams)
         _, self.handle = p3_batch_create([p.handle for p in self.plans], nstreams)
+
+    def launches(self, direction: int) -> int:
+        return p3_batch_launches(self.handle, direction)
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -126,6 +126,11 @@ def test_null_plan_calls(lib):
     assert P.p3_batch_destroy(None) == P.P3_OK
     assert P.p3_batch_ftran_r2c(None, None, None, None, None, check=False) == P.P3_ERR_INVALID
     assert P.p3_batch_btran_c2r(None, None, None, None, None, check=False) == P.P3_ERR_INVALID
+    assert P.p3_batch_wait_status(None) == P.P3_ERR_INVALID
+    assert P.p3_batch_set_wait_limits(None, 10, 0, check=False) == P.P3_ERR_INVALID
+    assert lib.p3_batch_launches(None, 0, ctypes.byref(n)) == P.P3_ERR_INVALID
+    st, h = P.p3_batch_create(None, -1, check=False)
+    assert st == P.P3_ERR_INVALID and h is None
 
 
 def test_binding_raises_when_library_missing(tmp_path, monkeypatch):
