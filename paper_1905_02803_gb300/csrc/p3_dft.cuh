@@ -20,6 +20,34 @@ template <class C> __device__ __forceinline__ C mk(decltype(C().x) x, decltype(C
 }
 template <class C> __device__ __forceinline__ C add(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C sub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+
+// FP32 complex add / subtract as one packed two-lane instruction
+// (add.rn.f32x2 / sub.rn.f32x2, sm_100 and later): the same two IEEE
+// round-to-nearest operations, in half the issue slots.
+__device__ __forceinline__ unsigned long long pk2(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r)
+{
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 add(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ float2 sub(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
 template <class C> __device__ __forceinline__ C mul(C a, C b)
 {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -42,14 +70,31 @@ template <class C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p
 // ---------------------------------------------------------------------------
 // Forward DFT butterflies of size R on v[0..R), exp(-2 pi i n m / R), in place.
 // ---------------------------------------------------------------------------
-template <class C, class T>
+// a + (-i) t and a - (-i) t (lanes swap, so no packed form)
+template <class C> __device__ __forceinline__ C add_mmi(C a, C t) { return mk<C>(a.x + t.y, a.y - t.x); }
+template <class C> __device__ __forceinline__ C sub_mmi(C a, C t) { return mk<C>(a.x - t.y, a.y + t.x); }
+// a times exp(-i pi / 4) and exp(-3 i pi / 4): two adds and one scale
+template <class C, class T> __device__ __forceinline__ C rot45(C a)
+{
+    const T h = (T)0.7071067811865476;
+    return mk<C>(h * (a.x + a.y), h * (a.y - a.x));
+}
+template <class C, class T> __device__ __forceinline__ C rot135(C a)
+{
+    const T h = (T)0.7071067811865476;
+    return mk<C>(h * (a.y - a.x), -h * (a.x + a.y));
+}
+
+// DFT4; with R2 the true a2 is -i times the given one (a rotation folded in)
+template <class C, class T, bool R2 = false>
 __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3)
 {
-    C s02 = add(a0, a2), d02 = sub(a0, a2), s13 = add(a1, a3), d13 = mmi(sub(a1, a3));
+    const C s02 = R2 ? add_mmi(a0, a2) : add(a0, a2), d02 = R2 ? sub_mmi(a0, a2) : sub(a0, a2);
+    const C s13 = add(a1, a3), t = sub(a1, a3);
     a0 = add(s02, s13);
     a2 = sub(s02, s13);
-    a1 = add(d02, d13);
-    a3 = sub(d02, d13);
+    a1 = add_mmi(d02, t);
+    a3 = sub_mmi(d02, t);
 }
 
 template <class C, class T, int R> struct Dft;
@@ -70,14 +115,12 @@ template <class C, class T> struct Dft<C, T, 4> {
 template <class C, class T> struct Dft<C, T, 8> {
     static __device__ __forceinline__ void run(C* v)
     {
-        const T h = (T)0.7071067811865476;  // sqrt(1/2)
         C u0 = add(v[0], v[4]), u1 = add(v[1], v[5]), u2 = add(v[2], v[6]), u3 = add(v[3], v[7]);
         C w0 = sub(v[0], v[4]), w1 = sub(v[1], v[5]), w2 = sub(v[2], v[6]), w3 = sub(v[3], v[7]);
-        w1 = mk<C>(h * (w1.x + w1.y), h * (w1.y - w1.x));   // * exp(-i pi/4)
-        w2 = mmi(w2);                                       // * exp(-i pi/2)
-        w3 = mk<C>(h * (w3.y - w3.x), -h * (w3.x + w3.y));  // * exp(-3i pi/4)
+        w1 = rot45<C, T>(w1);   // * exp(-i pi/4)
+        w3 = rot135<C, T>(w3);  // * exp(-3i pi/4)
         dft4<C, T>(u0, u1, u2, u3);
-        dft4<C, T>(w0, w1, w2, w3);
+        dft4<C, T, true>(w0, w1, w2, w3);  // w2 * exp(-i pi/2) folded in
         v[0] = u0; v[2] = u1; v[4] = u2; v[6] = u3;
         v[1] = w0; v[3] = w1; v[5] = w2; v[7] = w3;
     }
@@ -85,27 +128,32 @@ template <class C, class T> struct Dft<C, T, 8> {
 
 template <class C, class T> struct Dft<C, T, 16> {
     // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle exp(-2 pi i n2 k1/16),
-    // DFT4 over n2; the result X[k1 + 4 k2] lands in slot 4 k1 + k2.
-    static __device__ __forceinline__ void run(C* v)
+    // DFT4 over n2; the result X[k1 + 4 k2] lands in slot 4 k1 + k2.  With
+    // R8 the true v[8] is -i times the given one.
+    template <bool R8 = false> static __device__ __forceinline__ void run(C* v)
     {
-        const T c1 = (T)0.9238795325112867, s1 = (T)0.3826834323650898, h = (T)0.7071067811865476;
+        const T c1 = (T)0.9238795325112867, s1 = (T)0.3826834323650898;
+        dft4<C, T, R8>(v[0], v[4], v[8], v[12]);
 #pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) dft4<C, T>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+        for (int n2 = 1; n2 < 4; ++n2) dft4<C, T>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
         v[5] = rot(v[5], c1, -s1);    // n2=1,k1=1: W^1
-        v[9] = rot(v[9], h, -h);      // n2=1,k1=2: W^2
+        v[9] = rot45<C, T>(v[9]);     // n2=1,k1=2: W^2
         v[13] = rot(v[13], s1, -c1);  // n2=1,k1=3: W^3
-        v[6] = rot(v[6], h, -h);      // n2=2,k1=1: W^2
-        v[10] = mmi(v[10]);           // n2=2,k1=2: W^4
-        v[14] = rot(v[14], -h, -h);   // n2=2,k1=3: W^6
+        v[6] = rot45<C, T>(v[6]);     // n2=2,k1=1: W^2
+        // n2=2,k1=2: W^4 = -i, folded into the k1 = 2 DFT4 below
+        v[14] = rot135<C, T>(v[14]);  // n2=2,k1=3: W^6
         v[7] = rot(v[7], s1, -c1);    // n2=3,k1=1: W^3
-        v[11] = rot(v[11], -h, -h);   // n2=3,k1=2: W^6
+        v[11] = rot135<C, T>(v[11]);  // n2=3,k1=2: W^6
         v[15] = rot(v[15], -c1, s1);  // n2=3,k1=3: W^9
         // A[n2][k1] sits at v[n2 + 4 k1]; DFT4 over n2 for each k1
         C o[16];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
             C a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
-            dft4<C, T>(a0, a1, a2, a3);
+            if (k1 == 2)
+                dft4<C, T, true>(a0, a1, a2, a3);
+            else
+                dft4<C, T>(a0, a1, a2, a3);
             o[k1] = a0; o[k1 + 4] = a1; o[k1 + 8] = a2; o[k1 + 12] = a3;
         }
 #pragma unroll
@@ -193,13 +241,15 @@ template <class C, class T> struct Dft<C, T, 32> {
         for (int k = 0; k < 16; ++k) {
             u[k] = add(v[k], v[k + 16]);
             const C d = sub(v[k], v[k + 16]);
-            // angle pi k / 16: cos / sin from the first-octant table
+            // angle pi k / 16: cos / sin from the first-octant table; k = 0
+            // is 1, k = 8 is -i (folded into DFT16's first DFT4), k = 4 and
+            // 12 are the 45 and 135 degree rotations
             const T ck = k <= 8 ? c[k] : -c[16 - k];
             const T sk = k <= 8 ? c[8 - k] : c[k - 8];
-            w[k] = rot(d, ck, -sk);
+            w[k] = k == 0 || k == 8 ? d : k == 4 ? rot45<C, T>(d) : k == 12 ? rot135<C, T>(d) : rot(d, ck, -sk);
         }
         Dft<C, T, 16>::run(u);
-        Dft<C, T, 16>::run(w);
+        Dft<C, T, 16>::template run<true>(w);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             v[2 * k] = u[k];
