@@ -754,6 +754,16 @@ def _report_batch(steps, warmup, nstreams=16):
         return timed(g.replay)
 
     pbatch = P.Batch(plans, nstreams=0)
+    # the same grids with P3_FLAG_TUNE (radix order and tile height of every
+    # generic stage chosen by timing at plan creation)
+    tplans = [P.Plan(nx, ny, nz, precision="f32", layout="zyx", flags=P.P3_FLAG_TUNE) for nx, ny, nz in dims]
+    for tp in tplans:
+        tp.workspace()
+    tbatch = P.Batch(tplans, nstreams=nstreams)
+
+    def tuned():
+        tbatch.forward(xs, Xs)
+        tbatch.backward(Xs, ys)
 
     def persistent():
         pbatch.forward(xs, Xs)
@@ -765,10 +775,11 @@ def _report_batch(steps, warmup, nstreams=16):
     ms_batch_graph = graphed(batched)
     ms_pers = timed(persistent)
     ms_pers_graph = graphed(persistent)
+    ms_tuned_graph = graphed(tuned)
     pair_bytes = sum(sum(stage_model_bytes(nx, ny, nz, 4)) for nx, ny, nz in dims)
     peak, _ = peaks()
     roof_ms = pair_bytes / (peak * 1e9) * 1e3
-    best = min(ms, ms_graph, ms_batch, ms_batch_graph, ms_pers, ms_pers_graph)
+    best = min(ms, ms_graph, ms_batch, ms_batch_graph, ms_pers, ms_pers_graph, ms_tuned_graph)
     launches = sum(p.launches(0) + p.launches(1) for p in plans)
     pers_launches = pbatch.launches(0) + pbatch.launches(1)
     kinds = sorted({l.split()[2] for p in plans for l in p.describe().splitlines() if "kernel=" in l})
@@ -777,6 +788,7 @@ def _report_batch(steps, warmup, nstreams=16):
             "ms_batch_streams": round(ms_batch, 4), "ms_batch_streams_cuda_graph": round(ms_batch_graph, 4),
             "ms_persistent": round(ms_pers, 4), "ms_persistent_cuda_graph": round(ms_pers_graph, 4),
             "persistent_launches_per_step": pers_launches,
+            "ms_batch_streams_cuda_graph_tuned_plans": round(ms_tuned_graph, 4),
             "batch_streams": nstreams, "stage_model_bytes": pair_bytes, "hbm_roofline_ms": round(roof_ms, 4),
             "hbm_roofline_frac": round(roof_ms / best, 4), "launches_per_step": launches, "kernels": kinds}
 

@@ -119,13 +119,18 @@ typedef enum { P3_LAYOUT_ZYX = 0, P3_LAYOUT_XYZ = 1 } p3_layout;
  *                so the second stage reads the first one's output from L2.
  *                Its CTAs wait on one another with bounded waits; see
  *                p3_plan_wait_status().
- *              P3_FLAG_TUNE: for each direction with a plane-fused launch,
- *                time the fused launch at a few queue lags and the separate
- *                X and Y launches once, here, and keep the fastest (all give
- *                the same result).  Allocates two buffers of the transform's
- *                size plus a workspace for the duration of the call, so plan
- *                creation takes milliseconds to a second; the timings appear
- *                in p3_plan_describe().
+ *              P3_FLAG_TUNE: time candidates here and keep the fastest,
+ *                the timings appearing in p3_plan_describe():
+ *                - each stage of the generic kernel (lengths that are not
+ *                  powers of two, Bluestein lines excepted) under a few
+ *                  orders of its radices and tile heights (the same
+ *                  transform, rounded in another order);
+ *                - for each direction with a plane-fused launch, the fused
+ *                  launch at a few queue lags and the separate X and Y
+ *                  launches (the same result).
+ *                Allocates buffers of the transform's size for the duration
+ *                of the call, so plan creation takes milliseconds to a
+ *                second.
  *              P3_FLAG_NO_TMA: load the Z stages' input tiles with ordinary
  *                loads instead of tensor-memory-access (TMA) copies: the
  *                forward ZYX-store stage (FP32 lines of 256 .. 2048 points)

@@ -476,6 +476,116 @@ static p3_status tune(p3_plan P, std::vector<Stage> (&unfused)[3], std::string& 
     return rc;
 }
 
+// P3_FLAG_TUNE for the generic stages (lengths that are not powers of two,
+// Bluestein lines excepted): time each stage alone under a few radix orders
+// of its factorisation and tile heights B, B / 2, B / 4 on temporary
+// buffers, and keep the fastest.  Any order is the same DFT with the same
+// root table; only rounding differs.
+static p3_status tune_generic(p3_plan P, std::string& report)
+{
+    const size_t rowr = P->padded ? 2 * (size_t)P->H : (size_t)P->nx;
+    const size_t nreal = rowr * P->ny * P->nz * (P->csize / 2);
+    const size_t ncplx = (size_t)P->H * P->ny * P->nz * P->csize;
+    const size_t nbuf = std::max(std::max(nreal, ncplx), P->ws_bytes) + 256;
+    bool any = false;
+    for (int d = 0; d < 2; ++d)
+        for (const Stage& st : P->st[d])
+            if (!st.fused && st.a.kern == p3::KIND_GENERIC && !st.a.blue && st.a.op != p3::OP_COPY && st.a.npass > 1)
+                any = true;
+    if (!any) return P3_OK;
+    void* buf[3] = {NULL, NULL, NULL};
+    cudaStream_t sm = NULL;
+    cudaEvent_t e0 = NULL, e1 = NULL;
+    p3_status rc = P3_OK;
+    for (int i = 0; i < 3 && rc == P3_OK; ++i)
+        if (cudaMalloc(&buf[i], nbuf) != cudaSuccess) rc = P3_ERR_NOMEM;
+    for (int i = 0; i < 3 && rc == P3_OK; ++i)
+        if (cudaMemset(buf[i], 0x3c, nbuf) != cudaSuccess) rc = P3_ERR_CUDA;
+    if (rc == P3_OK && (cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = P3_ERR_CUDA;
+    for (int d = 0; d < 2 && rc == P3_OK; ++d) {
+        for (size_t si = 0; si < P->st[d].size() && rc == P3_OK; ++si) {
+            Stage& st = P->st[d][si];
+            StageArgs& a0 = st.a;
+            if (st.fused || a0.kern != p3::KIND_GENERIC || a0.blue || a0.op == p3::OP_COPY || a0.npass <= 1) continue;
+            // candidate radix orders: as factored, reversed, ascending, and
+            // each rotation of the factored order
+            std::vector<std::vector<int>> orders;
+            std::vector<int> base(a0.rad, a0.rad + a0.npass);
+            auto add_order = [&](const std::vector<int>& o) {
+                if (std::find(orders.begin(), orders.end(), o) == orders.end()) orders.push_back(o);
+            };
+            add_order(base);
+            add_order(std::vector<int>(base.rbegin(), base.rend()));
+            std::vector<int> asc = base;
+            std::sort(asc.begin(), asc.end());
+            add_order(asc);
+            for (size_t k = 1; k < base.size(); ++k) {
+                std::vector<int> rot(base.begin() + k, base.end());
+                rot.insert(rot.end(), base.begin(), base.begin() + k);
+                add_order(rot);
+            }
+            float best = 1e30f;
+            StageArgs pick = a0;
+            std::string line = std::string(d == 0 ? "fwd " : "bwd ") + st.name + " tuned:";
+            for (const auto& o : orders) {
+                for (int shrink = 0; shrink < 3 && rc == P3_OK; ++shrink) {
+                    StageArgs a = a0;
+                    for (size_t k = 0; k < o.size(); ++k) a.rad[k] = o[k];
+                    generic_tile_setup(a, P->csize);
+                    if ((a.B >> shrink) < 1) break;
+                    if (shrink) {
+                        a.B >>= shrink;
+                        const bool elem = a.in_elem_fast || a.out_elem_fast;
+                        a.LDB = (elem && (a.B % 2 == 0)) ? a.B + 1 : a.B;
+                        a.threads = (a.B * a.tpl + 31) / 32 * 32;
+                        const int len = a.nfft > 0 ? a.nfft : 1;
+                        a.smem = 2 * (size_t)len * (size_t)a.LDB * P->csize;
+                    }
+                    a.src = buf[st.src];
+                    a.dst = buf[st.dst];
+                    a.err = P->derr;
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 4 && rc == P3_OK; ++rep) {
+                        if (rep == 1 && cudaEventRecord(e0, sm) != cudaSuccess) rc = P3_ERR_CUDA;
+                        const cudaError_t e = P->prec == P3_F32 ? p3::launch_stage_f32(a, sm) : p3::launch_stage_f64(a, sm);
+                        if (e != cudaSuccess) rc = P3_ERR_CUDA;
+                    }
+                    if (rc == P3_OK && (cudaEventRecord(e1, sm) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                        rc = P3_ERR_CUDA;
+                    if (rc != P3_OK) break;
+                    ms /= 3.f;
+                    std::string rs;
+                    for (size_t k = 0; k < o.size(); ++k) rs += (k ? "x" : "") + std::to_string(o[k]);
+                    char b[96];
+                    snprintf(b, sizeof(b), " %s/B%d=%.4fms", rs.c_str(), a.B, ms);
+                    line += b;
+                    if (ms < best) {
+                        best = ms;
+                        pick = a;
+                    }
+                }
+            }
+            if (rc != P3_OK) break;
+            pick.src = NULL;
+            pick.dst = NULL;
+            a0 = pick;
+            std::string rs;
+            for (int k = 0; k < a0.npass; ++k) rs += (k ? "x" : "") + std::to_string(a0.rad[k]);
+            report += line + " -> " + rs + "/B" + std::to_string(a0.B) + "\n";
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sm) cudaStreamDestroy(sm);
+    for (void* b : buf)
+        if (b) cudaFree(b);
+    cudaGetLastError();
+    return rc;
+}
+
 extern "C" {
 
 const char* p3_status_string(p3_status s)
@@ -852,6 +962,22 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     P->st_unfused[1] = unfused[1];
     // ---- autotuning (P3_FLAG_TUNE) -------------------------------------------
     std::string tuned;
+    if (flags & P3_FLAG_TUNE) {
+        rc = tune_generic(P, tuned);
+        if (rc != P3_OK) {
+            if (P->dtab) cudaFree(P->dtab);
+            if (P->derr) cudaFree(P->derr);
+            cudaGetLastError();
+            delete P;
+            return rc;
+        }
+    }
+    // the batched persistent launch starts from the tuned radix orders too
+    for (int d = 0; d < 2; ++d) {
+        bool fused = false;
+        for (const Stage& s : P->st[d]) fused = fused || s.fused;
+        if (!fused) P->st_unfused[d] = P->st[d];
+    }
     if ((flags & P3_FLAG_TUNE) && any_fused) {
         rc = tune(P, unfused, tuned);
         if (rc != P3_OK) {
