@@ -463,7 +463,12 @@ cudaError_t fused_launch(const PlaneArgs& f, cudaStream_t s)
     if (f.x.nlines <= 0 || f.nplanes <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(f.ctr, 0, sizeof(unsigned) * (size_t)(1 + f.nplanes), s);
     if (e != cudaSuccess) return e;
-    void* args[] = {const_cast<PlaneArgs*>(&f)};
+    PlaneArgs m = f;
+    line_magic(m.x.in, m.x.nlines);
+    line_magic(m.x.out, m.x.nlines);
+    line_magic(m.y.in, m.y.nlines);
+    line_magic(m.y.out, m.y.nlines);
+    void* args[] = {&m};
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)f.grid), dim3((unsigned)f.nt), args, f.smem, s);
 }
 

@@ -28,7 +28,26 @@ constexpr int kMaxLine = 4096;
 // counted in elements of the array's type (real or complex).
 struct LineMap {
     long long per, gstride, lstride, es;
+    // L / per as a multiply-high when pm != 0 (see line_magic)
+    unsigned pm;
+    int ps;
 };
+
+// Fills m.pm / m.ps so that L / per = (L * pm) >> ps for every line
+// 0 <= L < nlines (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994, Sect. 4, with 31-bit numerators:
+// l = ceil(log2 per), pm = floor(2^(31+l) / per) + 1 < 2^32, ps = 31 + l);
+// pm = 0 (plain division) when per or nlines does not fit in 31 bits.
+inline void line_magic(LineMap& m, long long nlines)
+{
+    m.pm = 0;
+    m.ps = 0;
+    if (m.per < 1 || m.per >= (1LL << 31) || nlines > (1LL << 31)) return;
+    int l = 0;
+    while ((1LL << l) < m.per) ++l;
+    m.pm = (unsigned)((1ULL << (31 + l)) / (unsigned long long)m.per + 1ULL);
+    m.ps = 31 + l;
+}
 
 // Stage kernel families (StageArgs::kern).
 enum KernelKind : int {
@@ -52,6 +71,16 @@ enum StageOp : int {
 };
 
 // Everything one stage kernel launch needs (passed by value).
+// Constants of one Stockham pass of the generic kernel (radix R after
+// passes whose radices multiply to Ns), computed on the host at launch by
+// generic_consts so that no thread divides by a run-time value.
+struct PassConsts {
+    int tstep;    // twiddle-table index of one unit of j mod Ns: (n / (Ns R)) * ts
+    int dq, dr;   // tpl / Ns, tpl mod Ns (a thread's step through the butterflies)
+    unsigned pm;  // t / Ns = (t * pm) >> ps (see line_magic)
+    int ps;
+};
+
 struct StageArgs {
     // TMA descriptor of the input tile (tma = 1): lines as the inner
     // dimension, line elements as the outer one; encoded per call with the
@@ -85,6 +114,8 @@ struct StageArgs {
     const void* chirp; // c[j] = exp(-pi i j^2 / nfft), j < nfft
     const void* bhat;  // DFT_m of the conjugate chirp filter, pre-scaled by 1/m
     const void* twm;   // exp(-2 pi i k / m), k < m
+    PassConsts pc[kMaxPasses];   // per pass of rad (generic kernel; filled at launch)
+    PassConsts mpc[kMaxPasses];  // per pass of mrad (Bluestein)
     size_t smem;       // dynamic shared memory bytes
     int threads;       // B * tpl
     int kern;          // KernelKind
@@ -102,6 +133,29 @@ struct StageArgs {
     // missing arrival and waits for its copies before it leaves
     int wait_extra;
 };
+
+inline void pass_consts(PassConsts* pc, int n, int npass, const int* rad, int tpl, int ts)
+{
+    long long ns = 1;
+    for (int p = 0; p < npass && p < kMaxPasses; ++p) {
+        const long long R = rad[p] > 0 ? rad[p] : 1;
+        pc[p].tstep = (int)((n / (ns * R)) * ts);
+        pc[p].dq = (int)(tpl / ns);
+        pc[p].dr = (int)(tpl % ns);
+        LineMap m = LineMap{ns, 0, 0, 0};
+        line_magic(m, 1LL << 31);
+        pc[p].pm = m.pm;
+        pc[p].ps = m.ps;
+        ns *= R;
+    }
+}
+
+// Fills the per-pass constants of a generic-kernel stage.
+inline void generic_consts(StageArgs& a)
+{
+    pass_consts(a.pc, a.nfft, a.npass, a.rad, a.tpl, a.twn / (a.nfft > 0 ? a.nfft : 1));
+    if (a.blue) pass_consts(a.mpc, a.m, a.mpass, a.mrad, a.tpl, 1);
+}
 
 // Launch one stage (defined in p3_kernels.cu).  Returns the launch error.
 cudaError_t launch_stage_f32(const StageArgs& a, cudaStream_t s);

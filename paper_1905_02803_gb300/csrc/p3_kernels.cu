@@ -29,27 +29,35 @@ namespace {
 // (j / Ns) Ns R + (j mod Ns) + r Ns.  Thread t of a line takes butterflies
 // t, t + tpl, ...; j / Ns and j mod Ns are updated incrementally.
 // ---------------------------------------------------------------------------
-template <class C, class T, int R>
+template <class C, class T, int R, bool SWAP = false>
 __device__ __forceinline__ void pass_pp(const C* src, C* dst, int LDB, int l, int t, int tpl, int n, int Ns,
-                                        const C* tw, int ts)
+                                        const PassConsts& c, const C* tw)
 {
     const int nb = n / R;
-    const int span = n / (Ns * R);
-    int q = t / Ns, rr = t - q * Ns;
-    const int dq = tpl / Ns, dr = tpl - dq * Ns;
+    const int istride = nb * LDB, ostride = Ns * LDB;  // slots between a butterfly's inputs / outputs
+    const int tstep = c.tstep;                         // table index of one unit of j mod Ns
+    int q = (int)(((unsigned long long)(unsigned)t * c.pm) >> c.ps), rr = t - q * Ns;
+    const int dq = c.dq, dr = c.dr;
     for (int j = t; j < nb; j += tpl) {
         C v[R];
+        const C* sp = src + j * LDB + l;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * LDB + l];
-        const int k = rr * span;
-        if (k) {
+        for (int r = 0; r < R; ++r) v[r] = SWAP ? swp(sp[r * istride]) : sp[r * istride];
+        if (rr) {
+            // exp(-2 pi i rr r / (Ns R)) = tw[rr r (n / (Ns R)) ts], the index
+            // kept as a running 32-bit sum
+            const int k = rr * tstep;
+            int idx = k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = mul(v[r], ldg(tw + (size_t)(k * r) * ts));
+            for (int r = 1; r < R; ++r) {
+                v[r] = mul(v[r], ldg(tw + idx));
+                idx += k;
+            }
         }
         Dft<C, T, R>::run(v);
-        const int base = q * Ns * R + rr;
+        C* dp = dst + (q * Ns * R + rr) * LDB + l;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * LDB + l] = v[r];
+        for (int r = 0; r < R; ++r) dp[r * ostride] = v[r];
         rr += dr;
         q += dq;
         if (rr >= Ns) {
@@ -59,10 +67,29 @@ __device__ __forceinline__ void pass_pp(const C* src, C* dst, int LDB, int l, in
     }
 }
 
-// All passes; the data starts in buf0 and the returned buffer holds the result.
+// All passes; the data starts in buf0 and the returned buffer holds the
+// result.  swap_in: the first pass swaps real and imaginary parts of its
+// inputs (the inverse transform as swp(DFT(swp(.)))).
+template <class C, class T, bool SWAP>
+__device__ __forceinline__ void pass_any(int R, const C* src, C* dst, int LDB, int l, int t, int tpl, int n, int Ns,
+                                         const PassConsts& c, const C* tw)
+{
+    switch (R) {
+    case 16: pass_pp<C, T, 16, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 8: pass_pp<C, T, 8, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 4: pass_pp<C, T, 4, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 2: pass_pp<C, T, 2, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 3: pass_pp<C, T, 3, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 5: pass_pp<C, T, 5, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    case 7: pass_pp<C, T, 7, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+    default: break;
+    }
+}
+
 template <class C, class T>
 __device__ __forceinline__ C* run_passes(C* buf0, C* buf1, int LDB, int l, int t, int tpl, bool act, int n,
-                                         int npass, const int* rad, const C* tw, int ts)
+                                         int npass, const int* rad, const PassConsts* pc, const C* tw,
+                                         bool swap_in = false)
 {
     int Ns = 1;
     C* src = buf0;
@@ -70,16 +97,10 @@ __device__ __forceinline__ C* run_passes(C* buf0, C* buf1, int LDB, int l, int t
     for (int p = 0; p < npass; ++p) {
         const int R = rad[p];
         if (act) {
-            switch (R) {
-            case 16: pass_pp<C, T, 16>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 8: pass_pp<C, T, 8>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 4: pass_pp<C, T, 4>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 2: pass_pp<C, T, 2>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 3: pass_pp<C, T, 3>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 5: pass_pp<C, T, 5>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            case 7: pass_pp<C, T, 7>(src, dst, LDB, l, t, tpl, n, Ns, tw, ts); break;
-            default: break;
-            }
+            if (p == 0 && swap_in)
+                pass_any<C, T, true>(R, src, dst, LDB, l, t, tpl, n, Ns, pc[p], tw);
+            else
+                pass_any<C, T, false>(R, src, dst, LDB, l, t, tpl, n, Ns, pc[p], tw);
         }
         __syncthreads();
         Ns *= R;
@@ -92,6 +113,12 @@ __device__ __forceinline__ C* run_passes(C* buf0, C* buf1, int LDB, int l, int t
 
 __device__ __forceinline__ long long line_base(const LineMap& m, long long L)
 {
+    if (m.pm) {  // L < 2^31: quotient by multiply-high (line_magic)
+        const unsigned u = (unsigned)L;
+        const unsigned q = (unsigned)(((unsigned long long)u * m.pm) >> m.ps);
+        const unsigned r = u - q * (unsigned)m.per;
+        return (long long)q * m.gstride + (long long)r * m.lstride;
+    }
     return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
 }
 
@@ -192,9 +219,8 @@ __device__ __forceinline__ const C* direct_src(const StageArgs& a, long long bas
 }
 
 template <class C>
-__device__ __forceinline__ void copy_async(C* dst, const C* src)
+__device__ __forceinline__ void copy_async(unsigned d, const C* src)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     if constexpr (sizeof(C) == 16)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
     else
@@ -206,56 +232,71 @@ __device__ __forceinline__ void copy_async_wait()
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// Transform result for bin k of the line whose slots start at sl (stride LDB).
-template <class C>
-__device__ __forceinline__ C result(const StageArgs& a, const C* sl, int LDB, int k)
+// Writes output elements e0, e0 + de, ... (< n_out) of one line, whose
+// transform result sits in slots sl[k * LDB]; the op's post-processing is
+// fixed at compile time and the global address advances as a running
+// pointer.
+template <int OP, bool BLUE, class C, class T>
+__device__ __forceinline__ void store_elems(const StageArgs& a, const C* sl, int LDB, long long base, int e0, int de)
 {
-    C v = sl[k * LDB];
-    if (a.blue) v = mul(ldg(static_cast<const C*>(a.chirp) + k), swp(v));
-    return v;
-}
-
-// Write output element e of a line.
-template <class C, class T>
-__device__ __forceinline__ void store_value(const StageArgs& a, const C* sl, int LDB, long long base, int e)
-{
-    const long long es = a.out.es;
-    switch (a.op) {
-    case OP_R2C_HALF: {
+    const int n_out = a.n_out;
+    const long long step = (long long)de * a.out.es;
+    const C* chirp = static_cast<const C*>(a.chirp);
+    // transform result for bin k (Bluestein: times the chirp, un-swapped)
+    auto res = [&](int k) -> C {
+        C v = sl[k * LDB];
+        if constexpr (BLUE) v = mul(ldg(chirp + k), swp(v));
+        return v;
+    };
+    if constexpr (OP == OP_R2C_HALF) {
         // F[k] = (Z[k] + conj Z[n-k]) / 2 - i exp(-2 pi i k / Nx) (Z[k] - conj Z[n-k]) / 2
         const int n = a.nfft;
-        const C zk = result(a, sl, LDB, e == n ? 0 : e);
-        const C zm = cnj(result(a, sl, LDB, e == 0 ? 0 : n - e));
-        const C p = mul(ldg(static_cast<const C*>(a.tw2) + e), sub(zk, zm));
-        const C F = mk<C>((T)0.5 * (zk.x + zm.x + p.y), (T)0.5 * (zk.y + zm.y - p.x));
-        static_cast<C*>(a.dst)[base + (long long)e * es] = F;
-        break;
+        const C* tw2 = static_cast<const C*>(a.tw2);
+        C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
+        for (int e = e0; e < n_out; e += de, p += step) {
+            const C zk = res(e == n ? 0 : e);
+            const C zm = cnj(res(e == 0 ? 0 : n - e));
+            const C q = mul(ldg(tw2 + e), sub(zk, zm));
+            *p = mk<C>((T)0.5 * (zk.x + zm.x + q.y), (T)0.5 * (zk.y + zm.y - q.x));
+        }
+    } else if constexpr (OP == OP_R2C_FULL || OP == OP_DCT1) {
+        C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
+        for (int e = e0; e < n_out; e += de, p += step) *p = res(e);
+    } else if constexpr (OP == OP_DST1) {
+        // Y[e] = i Z[e + 1] (forward sign: Z[k] = -2i sum x_j sin(pi k (j+1)/(n+1)))
+        C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
+        for (int e = e0; e < n_out; e += de, p += step) {
+            const C z = res(e + 1);
+            *p = mk<C>(-z.y, z.x);
+        }
+    } else if constexpr (OP == OP_C2R_HALF) {
+        // f[2j] = Re z[j], f[2j+1] = Im z[j]: one complex-sized store per j
+        C* p = reinterpret_cast<C*>(static_cast<T*>(a.dst) + base) + e0;
+        for (int e = e0; e < n_out; e += de, p += de) *p = swp(res(e));
+    } else if constexpr (OP == OP_C2R_FULL) {
+        T* p = static_cast<T*>(a.dst) + base + e0 * a.out.es;
+        for (int e = e0; e < n_out; e += de, p += step) *p = swp(res(e)).x;
+    } else {  // OP_C2C, OP_COPY
+        const bool sw = a.sign > 0;
+        C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
+        for (int e = e0; e < n_out; e += de, p += step) {
+            const C v = res(e);
+            *p = sw ? swp(v) : v;
+        }
     }
-    case OP_R2C_FULL:
-    case OP_DCT1:
-        static_cast<C*>(a.dst)[base + (long long)e * es] = result(a, sl, LDB, e);
-        break;
-    case OP_DST1: {  // Y[e] = i Z[e + 1] (forward sign: Z[k] = -2i sum x_j sin(pi k (j+1)/(n+1)))
-        const C z = result(a, sl, LDB, e + 1);
-        static_cast<C*>(a.dst)[base + (long long)e * es] = mk<C>(-z.y, z.x);
-        break;
-    }
-    case OP_C2R_HALF: {  // f[2j] = Re z[j], f[2j+1] = Im z[j]
-        const C z = swp(result(a, sl, LDB, e));
-        *reinterpret_cast<C*>(static_cast<T*>(a.dst) + base + 2 * (long long)e) = z;
-        break;
-    }
-    case OP_C2R_FULL: {
-        const C z = swp(result(a, sl, LDB, e));
-        static_cast<T*>(a.dst)[base + (long long)e * es] = z.x;
-        break;
-    }
-    default: {  // OP_C2C, OP_COPY
-        C v = result(a, sl, LDB, e);
-        if (a.sign > 0) v = swp(v);
-        static_cast<C*>(a.dst)[base + (long long)e * es] = v;
-        break;
-    }
+}
+
+template <bool BLUE, class C, class T>
+__device__ __forceinline__ void store_line(const StageArgs& a, const C* sl, int LDB, long long base, int e0, int de)
+{
+    switch (a.op) {
+    case OP_R2C_HALF: store_elems<OP_R2C_HALF, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    case OP_R2C_FULL: store_elems<OP_R2C_FULL, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    case OP_DCT1: store_elems<OP_DCT1, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    case OP_DST1: store_elems<OP_DST1, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    case OP_C2R_HALF: store_elems<OP_C2R_HALF, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    case OP_C2R_FULL: store_elems<OP_C2R_FULL, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
+    default: store_elems<OP_C2C, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     }
 }
 
@@ -291,41 +332,41 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     // their latencies overlap instead of adding up
     constexpr int KB = sizeof(T) == 4 ? 8 : 4;
     const C zero = mk<C>((T)0, (T)0);
+    // Lines of the tile and the elements a thread takes: with lanes walking
+    // elements, warp w takes lines w, w + nw, ... and lane e0 elements
+    // e0, e0 + 32, ...; otherwise thread tid takes line tid mod B, elements
+    // tid / B, tid / B + NT / B, ...
+    const bool sw_in = a.sign > 0 && (a.op == OP_C2C || a.op == OP_COPY);  // inverse: swapped input
     if (direct_load(a)) {
-        // every slot is a copy of one input value (nfill == nload); the
-        // thread's own copies are complete after the wait, so it applies the
-        // inverse's swap to exactly those slots before the barrier.  The c2r
-        // input F[0..n] is copied as it is (F[n] to the second buffer, unused
-        // until the first pass) and pre-twiddled in shared memory below.
-        const bool sw = a.sign > 0 && (a.op == OP_C2C || a.op == OP_COPY);
-        if (a.in_elem_fast) {
-            const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
-            const int ncopy = a.op == OP_C2R_HALF ? nload + 1 : nload;
-            for (int l = warp; l < B; l += nw) {
-                const long long L = L0 + l;
-                if (L >= a.nlines) break;
-                const long long base = line_base(a.in, L);
-                for (int e = lane; e < ncopy; e += 32)
-                    copy_async(e < nload ? s0 + (size_t)e * LDB + l : s1 + l, direct_src<C, T>(a, base, e));
-            }
-            copy_async_wait();
-            if (sw)
-                for (int l = warp; l < B; l += nw) {
-                    if (L0 + l >= a.nlines) break;
-                    for (int e = lane; e < nload; e += 32) s0[(size_t)e * LDB + l] = swp(s0[(size_t)e * LDB + l]);
-                }
-        } else {
-            const int l = tid & (B - 1);
+        // every slot is a copy of one input value (nfill == nload).  The
+        // inverse's real/imaginary swap is applied by the first pass (or,
+        // without passes, below); the c2r input F[0..n] is copied as it is
+        // (F[n] to the second buffer, unused until the first pass) and
+        // pre-twiddled in shared memory below.
+        const bool ef = a.in_elem_fast;
+        const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
+        const int e0 = ef ? tid & 31 : tid / B, de = ef ? 32 : NT / B;
+        const long long gstep = (long long)de * (a.op == OP_R2C_HALF ? 1 : a.in.es);  // complex values
+        const unsigned sstep = (unsigned)(de * LDB * (int)sizeof(C));
+        for (int l = l0; l < B; l += dl) {
             const long long L = L0 + l;
-            const int st = NT / B;
-            if (L < a.nlines) {
-                const long long base = line_base(a.in, L);
-                for (int e = tid / B; e < nload; e += st) copy_async(s0 + (size_t)e * LDB + l, direct_src<C, T>(a, base, e));
-                copy_async_wait();
-                if (sw)
-                    for (int e = tid / B; e < nload; e += st) s0[(size_t)e * LDB + l] = swp(s0[(size_t)e * LDB + l]);
-                if (a.op == OP_C2R_HALF && tid < B) copy_async(s1 + l, direct_src<C, T>(a, base, nload));
-                copy_async_wait();
+            if (L >= a.nlines) break;
+            const long long base = line_base(a.in, L);
+            const C* g = direct_src<C, T>(a, base, e0);
+            unsigned sa = (unsigned)__cvta_generic_to_shared(s0 + e0 * LDB + l);
+            for (int e = e0; e < nload; e += de) {
+                copy_async(sa, g);
+                g += gstep;
+                sa += sstep;
+            }
+            if (a.op == OP_C2R_HALF && e0 == 0)
+                copy_async((unsigned)__cvta_generic_to_shared(s1 + l), direct_src<C, T>(a, base, nload));
+        }
+        copy_async_wait();
+        if (sw_in && a.npass == 0) {
+            for (int l = l0; l < B; l += dl) {
+                if (L0 + l >= a.nlines) break;
+                for (int e = e0; e < nload; e += de) s0[e * LDB + l] = swp(s0[e * LDB + l]);
             }
         }
         if (a.op == OP_C2R_HALF) {
@@ -405,38 +446,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
         const int t = tid / B;
         const bool act = tid < B * a.tpl;
         if (!a.blue) {
-            s = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.nfft, a.npass, a.rad,
-                                 static_cast<const C*>(a.tw), a.twn / (a.nfft > 0 ? a.nfft : 1));
+            s = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.nfft, a.npass, a.rad, a.pc,
+                                 static_cast<const C*>(a.tw), sw_in && direct_load(a));
         } else {
             // Bluestein: DFT_m, pointwise product with the filter spectrum,
             // inverse DFT_m as swp(DFT_m(swp(.))); the 1/m is folded into bhat.
             const C* twm = static_cast<const C*>(a.twm);
-            C* x = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
+            C* x = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, a.mpc, twm);
             const C* bh = static_cast<const C*>(a.bhat);
             for (int i = tid; i < a.m * B; i += NT) {
                 const int k = i / B, ll = i - k * B;
                 x[k * LDB + ll] = swp(mul(x[k * LDB + ll], ldg(bh + k)));
             }
             __syncthreads();
-            s = run_passes<C, T>(x, x == s0 ? s1 : s0, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, twm, 1);
+            s = run_passes<C, T>(x, x == s0 ? s1 : s0, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, a.mpc, twm);
         }
     }
 
     // ---- store: shared memory -> HBM -----------------------------------
-    if (a.out_elem_fast) {
-        const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
-        for (int l = warp; l < B; l += nw) {
+    {
+        const bool ef = a.out_elem_fast;
+        const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
+        const int e0 = ef ? tid & 31 : tid / B, de = ef ? 32 : NT / B;
+        for (int l = l0; l < B; l += dl) {
             const long long L = L0 + l;
             if (L >= a.nlines) break;
             const long long base = line_base(a.out, L);
-            for (int e = lane; e < a.n_out; e += 32) store_value<C, T>(a, s + l, LDB, base, e);
-        }
-    } else {
-        const int l = tid & (B - 1);
-        const long long L = L0 + l;
-        if (L < a.nlines) {
-            const long long base = line_base(a.out, L);
-            for (int e = tid / B; e < a.n_out; e += NT / B) store_value<C, T>(a, s + l, LDB, base, e);
+            if (a.blue)
+                store_line<true, C, T>(a, s + l, LDB, base, e0, de);
+            else
+                store_line<false, C, T>(a, s + l, LDB, base, e0, de);
         }
     }
 }
@@ -450,11 +489,15 @@ __global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P
 }
 
 template <typename T>
-cudaError_t launch_stage(const StageArgs& a, cudaStream_t st)
+cudaError_t launch_stage(const StageArgs& a0, cudaStream_t st)
 {
-    if (a.nlines <= 0) return cudaSuccess;
-    const long long grid = (a.nlines + a.B - 1) / a.B;
+    if (a0.nlines <= 0) return cudaSuccess;
+    const long long grid = (a0.nlines + a0.B - 1) / a0.B;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    StageArgs a = a0;
+    line_magic(a.in, a.nlines);
+    line_magic(a.out, a.nlines);
+    generic_consts(a);
     stage_kernel<T><<<(unsigned)grid, a.threads, a.smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -122,8 +122,11 @@ cudaError_t pow2_launch(const StageArgs& a, bool f32, cudaStream_t st)
     if (a.nlines <= 0) return cudaSuccess;
     long long grid = (a.nlines + a.B - 1) / a.B;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    void* args[] = {const_cast<StageArgs*>(&a)};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(a.threads), args, a.smem, st);
+    StageArgs m = a;
+    line_magic(m.in, m.nlines);
+    line_magic(m.out, m.nlines);
+    void* args[] = {&m};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(m.threads), args, m.smem, st);
 }
 
 // cuTensorMapEncodeTiled, from the driver through the runtime (resolved once)

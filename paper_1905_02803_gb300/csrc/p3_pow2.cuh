@@ -101,6 +101,12 @@ template <int NT, int CSIZE, int E> struct MinBlocks {
 
 __device__ __forceinline__ long long lbase(const LineMap& m, long long L)
 {
+    if (m.pm) {  // L < 2^31: quotient by multiply-high (line_magic)
+        const unsigned u = (unsigned)L;
+        const unsigned q = (unsigned)(((unsigned long long)u * m.pm) >> m.ps);
+        const unsigned r = u - q * (unsigned)m.per;
+        return (long long)q * m.gstride + (long long)r * m.lstride;
+    }
     return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
 }
 
