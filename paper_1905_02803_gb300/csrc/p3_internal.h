@@ -20,6 +20,11 @@ constexpr int kMaxPasses = 14;
 constexpr int kVmax = P3_GEN_VMAX;
 // Threads per CTA never exceed this (matches __launch_bounds__).
 constexpr int kMaxThreads = 256;
+// Threads per CTA of the generic stage kernel (its own launch bounds).
+#ifndef P3_GEN_MAXT
+#define P3_GEN_MAXT 256
+#endif
+constexpr int kGenThreads = P3_GEN_MAXT;
 // Longest native line; Bluestein lines need a padded length <= this too.
 constexpr int kMaxLine = 4096;
 

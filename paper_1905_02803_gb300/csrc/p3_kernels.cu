@@ -300,13 +300,15 @@ __device__ __forceinline__ void store_line(const StageArgs& a, const C* sl, int 
     }
 }
 
-// Resident CTAs per SM the register allocation is sized for.  FP32: four
-// 256-thread CTAs (64 registers, a few bytes of spill) hide the strided loads
-// and stores of the generic path better than two CTAs at 96 registers (about
-// 20 % faster on 7-smooth grids); five gain nothing more.  FP64 stays at two:
-// three CTAs spill several hundred bytes for a gain of about 2 %.
+// Resident CTAs per SM the register allocation is sized for.  FP32: three
+// 256-thread CTAs (85 registers).  Measured on 7-smooth grids (384^3 pair,
+// 64-grid batch): 0.99 / 8.44 ms against 1.09 / 8.67 ms with four CTAs at 64
+// registers (which spill) and 1.29 / 9.49 ms with two at 128 -- with the
+// asynchronous tile loads the kernel needs registers more than a fourth CTA.
+// FP64 stays at two: three CTAs spill several hundred bytes for a gain of
+// about 2 %.
 #ifndef P3_GEN_MINB
-#define P3_GEN_MINB 4
+#define P3_GEN_MINB 3
 #endif
 #ifndef P3_GEN_MINB_F64
 #define P3_GEN_MINB_F64 2
@@ -481,7 +483,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P3_GEN_MINB_F64))
+__global__ void __launch_bounds__(kGenThreads, (sizeof(T) == 4 ? P3_GEN_MINB : P3_GEN_MINB_F64))
     stage_kernel(const __grid_constant__ StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -302,11 +302,15 @@ p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
 // Lines per CTA, pitch, threads and shared memory of a stage.
 // Tile shape of the generic kernel: B lines per CTA (a power of two) so that
 // the ping-pong buffers fit 100 KB, LDB the shared-memory pitch.
-void generic_tile_setup(StageArgs& a, size_t csize, size_t cap = 100 * 1024)
+// Shared memory a generic-kernel tile may take (bytes).
+#ifndef P3_GEN_SMEM_CAP
+#define P3_GEN_SMEM_CAP (100 * 1024)
+#endif
+void generic_tile_setup(StageArgs& a, size_t csize, size_t cap = P3_GEN_SMEM_CAP, int maxt = p3::kGenThreads)
 {
     const int len = a.blue ? a.m : (a.nfft > 0 ? a.nfft : 1);
     const bool elem = a.in_elem_fast || a.out_elem_fast;
-    int B = pow2_floor(p3::kMaxThreads / a.tpl);
+    int B = pow2_floor(maxt / a.tpl);
     if (B < 1) B = 1;
     while (B > 1 && 2 * (size_t)len * (size_t)(B + 1) * csize > cap) B /= 2;
     const long long lim = pow2_ceil(a.nlines > 0 ? a.nlines : 1);
@@ -1319,7 +1323,7 @@ p3_status generic_stages(p3_plan P, int dir, std::vector<GenericStage>& out)
         }
         // tiles of at most P3_BATCH_SMEM bytes, so that the batched kernel
         // keeps its resident CTAs whatever stage it runs
-        generic_tile_setup(g.a, P->csize, P3_BATCH_SMEM);
+        generic_tile_setup(g.a, P->csize, P3_BATCH_SMEM, p3::kMaxThreads);
         g.src = s.src;
         g.dst = s.dst;
         out.push_back(g);
