@@ -109,8 +109,9 @@ static p3_status build_tasks(p3_batch b, int d)
             memset(&t, 0, sizeof(t));
             t.a = g.a;
             t.a.err = b->derr;
-            p3::line_magic(t.a.in, t.a.nlines);
-            p3::line_magic(t.a.out, t.a.nlines);
+            const long long nl = t.a.nrows > t.a.nlines ? t.a.nrows : t.a.nlines;  // pair ops index rows
+            p3::line_magic(t.a.in, nl);
+            p3::line_magic(t.a.out, nl);
             p3::generic_consts(t.a);
             t.first = next;
             t.ntiles = g.a.nlines > 0 ? (g.a.nlines + g.a.B - 1) / g.a.B : 0;

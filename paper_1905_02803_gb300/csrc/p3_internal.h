@@ -67,9 +67,10 @@ enum KernelKind : int {
 enum StageOp : int {
     OP_C2C = 0,       // complex line -> complex line
     OP_R2C_HALF = 1,  // even Nx: length Nx/2 complex FFT of (f[2j], f[2j+1]) + real split
-    OP_R2C_FULL = 2,  // odd Nx: complex FFT of the real line, keep H bins
+    OP_R2C_PAIR = 2,  // odd Nx: two real rows as one complex line f1 + i f2, FFT, both spectra split off
     OP_C2R_HALF = 3,  // even Nx: Hermitian pre-twiddle + length Nx/2 complex FFT
-    OP_C2R_FULL = 4,  // odd Nx: weighted, zero-padded line, complex FFT, real part
+    OP_C2R_PAIR = 4,  // odd Nx: two half spectra as one line X1 + i X2 (both Hermitian-extended),
+                      // FFT, real and imaginary parts
     OP_DCT1 = 5,      // Chebyshev: even extension to 2M points, FFT, first M+1 bins
     OP_COPY = 6,      // empty transform (re-orientation only)
     OP_DST1 = 7,      // sine: odd extension to 2(n+1) points, FFT, i times bins 1..n
@@ -95,6 +96,7 @@ struct StageArgs {
     void* dst;
     LineMap in, out;
     long long nlines;
+    long long nrows;   // pair ops: real rows (line L holds rows 2L and 2L + 1 < nrows)
     int op;
     int n_in, n_out;   // points read / written per line
     int nfft;          // length of the complex DFT done on each line

@@ -122,21 +122,17 @@ __device__ __forceinline__ long long line_base(const LineMap& m, long long L)
     return (L / m.per) * m.gstride + (L % m.per) * m.lstride;
 }
 
-// Value placed in shared-memory slot e of a line before the FFT.
-template <class C, class T>
+// Value placed in shared-memory slot e of a line before the FFT (the op
+// fixed at compile time).
+template <int OP, bool BLUE, class C, class T>
 __device__ __forceinline__ C load_value(const StageArgs& a, long long base, int e)
 {
     const long long es = a.in.es;
     C v;
-    switch (a.op) {
+    switch (OP) {
     case OP_R2C_HALF: {  // z[j] = f[2j] + i f[2j+1]; rows are contiguous
         const T* f = static_cast<const T*>(a.src);
         v = *reinterpret_cast<const C*>(f + base + 2 * (long long)e);
-        break;
-    }
-    case OP_R2C_FULL: {
-        const T* f = static_cast<const T*>(a.src);
-        v = mk<C>(f[base + (long long)e * es], (T)0);
         break;
     }
     case OP_C2R_HALF: {
@@ -153,18 +149,6 @@ __device__ __forceinline__ C load_value(const StageArgs& a, long long base, int 
         const C ze = add(A, B);
         const C zo = mul(sub(A, B), cnj(ldg(static_cast<const C*>(a.tw2) + e)));
         v = swp(mk<C>(ze.x - zo.y, ze.y + zo.x));
-        break;
-    }
-    case OP_C2R_FULL: {
-        // weighted, zero-padded half spectrum: w_0 = 1, w_k = 2 (k < H), 0 above
-        const C* F = static_cast<const C*>(a.src);
-        if (e < a.n_in) {
-            v = F[base + (long long)e * es];
-            if (e) v = scl(v, (T)2);
-        } else {
-            v = mk<C>((T)0, (T)0);
-        }
-        v = swp(v);
         break;
     }
     case OP_DCT1: {  // even extension y[e] = x[e] (e <= M), x[2M - e] (e > M)
@@ -194,8 +178,150 @@ __device__ __forceinline__ C load_value(const StageArgs& a, long long base, int 
         break;
     }
     }
-    if (a.blue) v = mul(v, ldg(static_cast<const C*>(a.chirp) + e));
+    if constexpr (BLUE) v = mul(v, ldg(static_cast<const C*>(a.chirp) + e));
     return v;
+}
+
+// Fills slots e0, e0 + de, ... (< nload) of line l from its input at base:
+// KB loads of a thread are issued before any of them is stored, so their
+// latencies overlap instead of adding up; slots at or past nfill are zero.
+template <int OP, bool BLUE, class C, class T>
+__device__ __forceinline__ void load_elems(const StageArgs& a, C* s0, int LDB, int l, long long base, int e0, int de,
+                                           int nload, int nfill)
+{
+    constexpr int KB = sizeof(T) == 4 ? 8 : 4;
+    const C zero = mk<C>((T)0, (T)0);
+    for (int eb = e0; eb < nload; eb += de * KB) {
+        C w[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            const int e = eb + de * k;
+            w[k] = e < nfill ? load_value<OP, BLUE, C, T>(a, base, e) : zero;
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+            if (eb + de * k < nload) s0[(eb + de * k) * LDB + l] = w[k];
+    }
+}
+
+template <bool BLUE, class C, class T>
+__device__ __forceinline__ void load_line(const StageArgs& a, C* s0, int LDB, int l, long long base, int e0, int de,
+                                          int nload, int nfill)
+{
+    switch (a.op) {
+    case OP_R2C_HALF: load_elems<OP_R2C_HALF, BLUE, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill); break;
+    case OP_C2R_HALF: load_elems<OP_C2R_HALF, BLUE, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill); break;
+    case OP_DCT1: load_elems<OP_DCT1, BLUE, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill); break;
+    case OP_DST1: load_elems<OP_DST1, BLUE, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill); break;
+    default: load_elems<OP_C2C, BLUE, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill); break;
+    }
+}
+
+// Odd real rows in pairs (the two-for-one real transform): line L of a
+// pair op holds real rows 2L and 2L + 1 (the second absent, i.e. zero, when
+// 2L + 1 = nrows), with bases b0 and b1 in the input (load) or output
+// (store).
+//
+// Forward load: slot e = f1[e] + i f2[e].
+// Inverse load: for k < H the half spectra give Z[k] = X1[k] + i X2[k] and
+// Z[N-k] = conj X1[k] + i conj X2[k] (k >= 1; N odd, so k and N - k cover
+// every bin once; the imaginary parts of X1[0] and X2[0] are dropped), swapped
+// for the inverse FFT.  Then Re and Im of the inverse transform are the
+// weighted-real C2R of X1 and of X2 (Sect. 3.2's complex-to-real transform).
+template <int OP, bool BLUE, class C, class T>
+__device__ __forceinline__ void pair_load(const StageArgs& a, C* s0, int LDB, int l, long long b0, long long b1,
+                                          bool has2, int e0, int de, int nload, int nfill)
+{
+    const long long es = a.in.es;
+    const C zero = mk<C>((T)0, (T)0);
+    const C* chirp = static_cast<const C*>(a.chirp);
+    if constexpr (OP == OP_R2C_PAIR) {
+        constexpr int KB = sizeof(T) == 4 ? 8 : 4;
+        const T* f = static_cast<const T*>(a.src);
+        for (int eb = e0; eb < nload; eb += de * KB) {
+            C w[KB];
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                const int e = eb + de * k;
+                w[k] = zero;
+                if (e < nfill) {
+                    w[k].x = f[b0 + e * es];
+                    if (has2) w[k].y = f[b1 + e * es];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                const int e = eb + de * k;
+                if (e < nload) s0[e * LDB + l] = (BLUE && e < nfill) ? mul(w[k], ldg(chirp + e)) : w[k];
+            }
+        }
+    } else {  // OP_C2R_PAIR: k < H = n_in
+        constexpr int KB = sizeof(T) == 4 ? 4 : 2;
+        const C* F = static_cast<const C*>(a.src);
+        const int H = a.n_in, N = a.nfft;
+        for (int kb = e0; kb < H; kb += de * KB) {
+            C A[KB], Bv[KB];
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int k = kb + de * u;
+                A[u] = zero;
+                Bv[u] = zero;
+                if (k < H) {
+                    A[u] = F[b0 + k * es];
+                    if (has2) Bv[u] = F[b1 + k * es];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int k = kb + de * u;
+                if (k >= H) continue;
+                if (k == 0) {
+                    A[u].y = (T)0;
+                    Bv[u].y = (T)0;
+                }
+                C zk = swp(mk<C>(A[u].x - Bv[u].y, A[u].y + Bv[u].x));
+                if constexpr (BLUE) zk = mul(zk, ldg(chirp + k));
+                s0[k * LDB + l] = zk;
+                if (k > 0) {
+                    C zm = swp(mk<C>(A[u].x + Bv[u].y, Bv[u].x - A[u].y));
+                    if constexpr (BLUE) zm = mul(zm, ldg(chirp + (N - k)));
+                    s0[(N - k) * LDB + l] = zm;
+                }
+            }
+        }
+        for (int e = nfill + e0; e < nload; e += de) s0[e * LDB + l] = zero;  // Bluestein padding
+    }
+}
+
+// Forward store: X1[k] = (Z[k] + conj Z[N-k]) / 2 and X2[k] = -i (Z[k] -
+// conj Z[N-k]) / 2 for k < H.  Inverse store: f1[j] = Re z[j], f2[j] = Im z[j].
+template <int OP, bool BLUE, class C, class T>
+__device__ __forceinline__ void pair_store(const StageArgs& a, const C* sl, int LDB, long long b0, long long b1,
+                                           bool has2, int e0, int de)
+{
+    const long long es = a.out.es;
+    const C* chirp = static_cast<const C*>(a.chirp);
+    auto res = [&](int k) -> C {
+        C v = sl[k * LDB];
+        if constexpr (BLUE) v = mul(ldg(chirp + k), swp(v));
+        return v;
+    };
+    if constexpr (OP == OP_R2C_PAIR) {
+        const int N = a.nfft;
+        C* X = static_cast<C*>(a.dst);
+        for (int k = e0; k < a.n_out; k += de) {
+            const C zk = res(k), zm = res(k == 0 ? 0 : N - k);
+            X[b0 + k * es] = mk<C>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            if (has2) X[b1 + k * es] = mk<C>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+        }
+    } else {  // OP_C2R_PAIR
+        T* f = static_cast<T*>(a.dst);
+        for (int j = e0; j < a.n_out; j += de) {
+            const C w = swp(res(j));
+            f[b0 + j * es] = w.x;
+            if (has2) f[b1 + j * es] = w.y;
+        }
+    }
 }
 
 // Ops whose load is a plain copy of one complex value (no pre-processing
@@ -259,7 +385,7 @@ __device__ __forceinline__ void store_elems(const StageArgs& a, const C* sl, int
             const C q = mul(ldg(tw2 + e), sub(zk, zm));
             *p = mk<C>((T)0.5 * (zk.x + zm.x + q.y), (T)0.5 * (zk.y + zm.y - q.x));
         }
-    } else if constexpr (OP == OP_R2C_FULL || OP == OP_DCT1) {
+    } else if constexpr (OP == OP_DCT1) {
         C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
         for (int e = e0; e < n_out; e += de, p += step) *p = res(e);
     } else if constexpr (OP == OP_DST1) {
@@ -273,9 +399,6 @@ __device__ __forceinline__ void store_elems(const StageArgs& a, const C* sl, int
         // f[2j] = Re z[j], f[2j+1] = Im z[j]: one complex-sized store per j
         C* p = reinterpret_cast<C*>(static_cast<T*>(a.dst) + base) + e0;
         for (int e = e0; e < n_out; e += de, p += de) *p = swp(res(e));
-    } else if constexpr (OP == OP_C2R_FULL) {
-        T* p = static_cast<T*>(a.dst) + base + e0 * a.out.es;
-        for (int e = e0; e < n_out; e += de, p += step) *p = swp(res(e)).x;
     } else {  // OP_C2C, OP_COPY
         const bool sw = a.sign > 0;
         C* p = static_cast<C*>(a.dst) + base + e0 * a.out.es;
@@ -291,11 +414,9 @@ __device__ __forceinline__ void store_line(const StageArgs& a, const C* sl, int 
 {
     switch (a.op) {
     case OP_R2C_HALF: store_elems<OP_R2C_HALF, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
-    case OP_R2C_FULL: store_elems<OP_R2C_FULL, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     case OP_DCT1: store_elems<OP_DCT1, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     case OP_DST1: store_elems<OP_DST1, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     case OP_C2R_HALF: store_elems<OP_C2R_HALF, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
-    case OP_C2R_FULL: store_elems<OP_C2R_FULL, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     default: store_elems<OP_C2C, BLUE, C, T>(a, sl, LDB, base, e0, de); break;
     }
 }
@@ -323,6 +444,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int B = a.B, LDB = a.LDB;
+    const int lb = __ffs(B) - 1;  // B is a power of two: x / B = x >> lb
     const long long L0 = tile * B;
     const int nload = a.blue ? a.m : a.nfft;  // slots filled per line
     const int nfill = a.blue ? a.nfft : nload;  // slots taken from the input
@@ -330,10 +452,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     C* s1 = s0 + (size_t)nload * LDB;  // second buffer of the ping-pong passes
 
     // ---- load: HBM -> shared memory ------------------------------------
-    // KB loads of a thread are issued before any of them is stored, so
-    // their latencies overlap instead of adding up
-    constexpr int KB = sizeof(T) == 4 ? 8 : 4;
-    const C zero = mk<C>((T)0, (T)0);
     // Lines of the tile and the elements a thread takes: with lanes walking
     // elements, warp w takes lines w, w + nw, ... and lane e0 elements
     // e0, e0 + 32, ...; otherwise thread tid takes line tid mod B, elements
@@ -347,7 +465,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
         // pre-twiddled in shared memory below.
         const bool ef = a.in_elem_fast;
         const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
-        const int e0 = ef ? tid & 31 : tid / B, de = ef ? 32 : NT / B;
+        const int e0 = ef ? tid & 31 : tid >> lb, de = ef ? 32 : NT >> lb;
         const long long gstep = (long long)de * (a.op == OP_R2C_HALF ? 1 : a.in.es);  // complex values
         const unsigned sstep = (unsigned)(de * LDB * (int)sizeof(C));
         for (int l = l0; l < B; l += dl) {
@@ -379,7 +497,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
             const int n = a.nfft, half = n / 2 + 1;
             const C* tw2 = static_cast<const C*>(a.tw2);
             for (int i = tid; i < B * half; i += NT) {
-                const int l = i & (B - 1), k = i / B;
+                const int l = i & (B - 1), k = i >> lb;
                 if (L0 + l >= a.nlines) continue;
                 const int m = n - k;  // partner slot (F[n] for k = 0)
                 C Fk = s0[(size_t)k * LDB + l];
@@ -402,41 +520,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
                 }
             }
         }
-    } else if (a.in_elem_fast) {
-        const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
-        for (int l = warp; l < B; l += nw) {
+    } else {
+        const bool ef = a.in_elem_fast;
+        const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
+        const int e0 = ef ? tid & 31 : tid >> lb, de = ef ? 32 : NT >> lb;
+        const bool pair = a.op == OP_R2C_PAIR || a.op == OP_C2R_PAIR;
+        for (int l = l0; l < B; l += dl) {
             const long long L = L0 + l;
             if (L >= a.nlines) break;
-            const long long base = line_base(a.in, L);
-            for (int e0 = lane; e0 < nload; e0 += 32 * KB) {
-                C w[KB];
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    const int e = e0 + 32 * k;
-                    w[k] = e < nfill ? load_value<C, T>(a, base, e) : zero;
+            if (pair) {
+                const bool has2 = 2 * L + 1 < a.nrows;
+                const long long b0 = line_base(a.in, 2 * L), b1 = has2 ? line_base(a.in, 2 * L + 1) : b0;
+                if (a.op == OP_R2C_PAIR) {
+                    if (a.blue) pair_load<OP_R2C_PAIR, true, C, T>(a, s0, LDB, l, b0, b1, has2, e0, de, nload, nfill);
+                    else pair_load<OP_R2C_PAIR, false, C, T>(a, s0, LDB, l, b0, b1, has2, e0, de, nload, nfill);
+                } else {
+                    if (a.blue) pair_load<OP_C2R_PAIR, true, C, T>(a, s0, LDB, l, b0, b1, has2, e0, de, nload, nfill);
+                    else pair_load<OP_C2R_PAIR, false, C, T>(a, s0, LDB, l, b0, b1, has2, e0, de, nload, nfill);
                 }
-#pragma unroll
-                for (int k = 0; k < KB; ++k)
-                    if (e0 + 32 * k < nload) s0[(e0 + 32 * k) * LDB + l] = w[k];
+                continue;
             }
-        }
-    } else {
-        const int l = tid & (B - 1);
-        const long long L = L0 + l;
-        if (L < a.nlines) {
             const long long base = line_base(a.in, L);
-            const int st = NT / B;
-            for (int e0 = tid / B; e0 < nload; e0 += st * KB) {
-                C w[KB];
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    const int e = e0 + st * k;
-                    w[k] = e < nfill ? load_value<C, T>(a, base, e) : zero;
-                }
-#pragma unroll
-                for (int k = 0; k < KB; ++k)
-                    if (e0 + st * k < nload) s0[(e0 + st * k) * LDB + l] = w[k];
-            }
+            if (a.blue)
+                load_line<true, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill);
+            else
+                load_line<false, C, T>(a, s0, LDB, l, base, e0, de, nload, nfill);
         }
     }
     __syncthreads();
@@ -445,7 +553,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     C* s = s0;
     {
         const int l = tid & (B - 1);
-        const int t = tid / B;
+        const int t = tid >> lb;
         const bool act = tid < B * a.tpl;
         if (!a.blue) {
             s = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.nfft, a.npass, a.rad, a.pc,
@@ -457,7 +565,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
             C* x = run_passes<C, T>(s0, s1, LDB, l, t, a.tpl, act, a.m, a.mpass, a.mrad, a.mpc, twm);
             const C* bh = static_cast<const C*>(a.bhat);
             for (int i = tid; i < a.m * B; i += NT) {
-                const int k = i / B, ll = i - k * B;
+                const int k = i >> lb, ll = i & (B - 1);
                 x[k * LDB + ll] = swp(mul(x[k * LDB + ll], ldg(bh + k)));
             }
             __syncthreads();
@@ -469,10 +577,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     {
         const bool ef = a.out_elem_fast;
         const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
-        const int e0 = ef ? tid & 31 : tid / B, de = ef ? 32 : NT / B;
+        const int e0 = ef ? tid & 31 : tid >> lb, de = ef ? 32 : NT >> lb;
+        const bool pair = a.op == OP_R2C_PAIR || a.op == OP_C2R_PAIR;
         for (int l = l0; l < B; l += dl) {
             const long long L = L0 + l;
             if (L >= a.nlines) break;
+            if (pair) {
+                const bool has2 = 2 * L + 1 < a.nrows;
+                const long long b0 = line_base(a.out, 2 * L), b1 = has2 ? line_base(a.out, 2 * L + 1) : b0;
+                if (a.op == OP_R2C_PAIR) {
+                    if (a.blue) pair_store<OP_R2C_PAIR, true, C, T>(a, s + l, LDB, b0, b1, has2, e0, de);
+                    else pair_store<OP_R2C_PAIR, false, C, T>(a, s + l, LDB, b0, b1, has2, e0, de);
+                } else {
+                    if (a.blue) pair_store<OP_C2R_PAIR, true, C, T>(a, s + l, LDB, b0, b1, has2, e0, de);
+                    else pair_store<OP_C2R_PAIR, false, C, T>(a, s + l, LDB, b0, b1, has2, e0, de);
+                }
+                continue;
+            }
             const long long base = line_base(a.out, L);
             if (a.blue)
                 store_line<true, C, T>(a, s + l, LDB, base, e0, de);
@@ -497,8 +618,9 @@ cudaError_t launch_stage(const StageArgs& a0, cudaStream_t st)
     const long long grid = (a0.nlines + a0.B - 1) / a0.B;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     StageArgs a = a0;
-    line_magic(a.in, a.nlines);
-    line_magic(a.out, a.nlines);
+    const long long nl = a.nrows > a.nlines ? a.nrows : a.nlines;  // pair ops index rows
+    line_magic(a.in, nl);
+    line_magic(a.out, nl);
     generic_consts(a);
     stage_kernel<T><<<(unsigned)grid, a.threads, a.smem, st>>>(a);
     return cudaGetLastError();

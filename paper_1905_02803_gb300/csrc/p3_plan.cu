@@ -340,9 +340,9 @@ const char* op_name(int op)
     switch (op) {
     case p3::OP_C2C: return "c2c";
     case p3::OP_R2C_HALF: return "r2c_half";
-    case p3::OP_R2C_FULL: return "r2c_full";
+    case p3::OP_R2C_PAIR: return "r2c_pair";
     case p3::OP_C2R_HALF: return "c2r_half";
-    case p3::OP_C2R_FULL: return "c2r_full";
+    case p3::OP_C2R_PAIR: return "c2r_pair";
     case p3::OP_DCT1: return "dct1";
     case p3::OP_DST1: return "dst1";
     default: return "copy";
@@ -684,6 +684,13 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         a.out_elem_fast = outm.es == 1;
         return a;
     };
+    // odd Nx: the X stage takes its real rows in pairs, one complex FFT of
+    // length Nx per two rows (line L: rows 2L and 2L + 1)
+    auto pair_args = [&](int op, int n_in, int n_out, int sign, LineMap in, LineMap outm) {
+        StageArgs a = base_args(op, n_in, n_out, nx, sign, (NY * NZ + 1) / 2, in, outm);
+        a.nrows = NY * NZ;
+        return a;
+    };
     auto push = [&](int dir, StageArgs a, int src, int dst, const char* name, double bytes, int twn) {
         Pending pd;
         if (rc != P3_OK) return;
@@ -717,8 +724,9 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
     {
         const bool half = nx % 2 == 0;
         const int nfft = half ? nx / 2 : nx;
-        StageArgs a = base_args(half ? p3::OP_R2C_HALF : p3::OP_R2C_FULL, nx, (int)H, nfft, -1, NY * NZ,
-                                rows(NY * NZ, RP), rows(NY * NZ, H));
+        StageArgs a = half ? base_args(p3::OP_R2C_HALF, nx, (int)H, nfft, -1, NY * NZ, rows(NY * NZ, RP),
+                                       rows(NY * NZ, H))
+                           : pair_args(p3::OP_R2C_PAIR, nx, (int)H, -1, rows(NY * NZ, RP), rows(NY * NZ, H));
         push(0, a, BUF_IN, zyx ? BUF_WS : BUF_OUT, "x_r2c", creal + ccplx, half ? nx : nx);
         const int work = zyx ? BUF_WS : BUF_OUT;
         if (ttype[1] == P3_FFT && ny > 1) {
@@ -774,8 +782,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         }
         const bool half = nx % 2 == 0;
         const int nfft = half ? nx / 2 : nx;
-        a = base_args(half ? p3::OP_C2R_HALF : p3::OP_C2R_FULL, (int)H, half ? nfft : nx, nfft, +1, NY * NZ,
-                      rows(NY * NZ, H), rows(NY * NZ, RP));
+        a = half ? base_args(p3::OP_C2R_HALF, (int)H, nfft, nfft, +1, NY * NZ, rows(NY * NZ, H), rows(NY * NZ, RP))
+                 : pair_args(p3::OP_C2R_PAIR, (int)H, nx, +1, rows(NY * NZ, H), rows(NY * NZ, RP));
         push(1, a, cur, BUF_OUT, "x_c2r", creal + ccplx, nx);
     }
     // ---- inverse with a user Z hook (EMPTY third dimension) ---------------
@@ -791,8 +799,8 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
         }
         const bool half = nx % 2 == 0;
         const int nfft = half ? nx / 2 : nx;
-        a = base_args(half ? p3::OP_C2R_HALF : p3::OP_C2R_FULL, (int)H, half ? nfft : nx, nfft, +1, NY * NZ,
-                      rows(NY * NZ, H), rows(NY * NZ, RP));
+        a = half ? base_args(p3::OP_C2R_HALF, (int)H, nfft, nfft, +1, NY * NZ, rows(NY * NZ, H), rows(NY * NZ, RP))
+                 : pair_args(p3::OP_C2R_PAIR, (int)H, nx, +1, rows(NY * NZ, H), rows(NY * NZ, RP));
         push(2, a, WORK, BUF_OUT, "x_c2r", creal + ccplx, nx);
     }
     if (rc != P3_OK) {

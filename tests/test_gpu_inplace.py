@@ -20,7 +20,8 @@ CASES = [
     (256, 64, 128, "f32", ("fft", "fft", "fft")),      # pow2 row and column kernels
     (1024, 32, 16, "f32", ("fft", "fft", "cheb")),
     (30, 12, 10, "f64", ("fft", "fft", "fft")),        # mixed-radix rows
-    (27, 9, 17, "f64", ("fft", "fft", "cheb")),        # odd Nx: full-length rows
+    (27, 9, 17, "f64", ("fft", "fft", "cheb")),        # odd Nx: rows in pairs, odd row count
+    (45, 7, 10, "f32", ("fft", "fft", "fft")),         # odd Nx: rows in pairs, even row count
     (128, 20, 24, "f64", ("fft", "empty", "fft")),
     (64, 16, 8, "f64", ("fft", "empty", "empty")),
     (2, 3, 2, "f64", ("fft", "fft", "fft")),
