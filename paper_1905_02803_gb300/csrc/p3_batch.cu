@@ -131,14 +131,27 @@ static p3_status build_tasks(p3_batch b, int d)
     b->smem[d] = smem;
     b->grid[d] = p3::batch_grid(smem);
     if (b->grid[d] < 1) return P3_ERR_CUDA;
+    // the tasks, then their compact scheduling fields
     const size_t tb = sizeof(p3::BatchTask) * std::max<size_t>(1, tasks.size());
-    if (cudaMalloc(&b->dtasks[d], tb) != cudaSuccess ||
+    std::vector<p3::BatchMeta> meta(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        meta[i].first = (unsigned)tasks[i].first;
+        meta[i].ntiles = (unsigned)tasks[i].ntiles;
+        meta[i].dep = tasks[i].dep;
+        meta[i].plan = tasks[i].plan;
+        meta[i].src = tasks[i].src;
+        meta[i].dst = tasks[i].dst;
+    }
+    const size_t mb = sizeof(p3::BatchMeta) * std::max<size_t>(1, tasks.size());
+    if (cudaMalloc(&b->dtasks[d], tb + mb) != cudaSuccess ||
         cudaMalloc(&b->dctr[d], sizeof(unsigned) * (size_t)(1 + b->ntasks[d])) != cudaSuccess) {
         cudaGetLastError();
         return P3_ERR_NOMEM;
     }
-    if (!tasks.empty() && cudaMemcpy(b->dtasks[d], tasks.data(), sizeof(p3::BatchTask) * tasks.size(),
-                                     cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (!tasks.empty() && (cudaMemcpy(b->dtasks[d], tasks.data(), sizeof(p3::BatchTask) * tasks.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess ||
+                           cudaMemcpy(reinterpret_cast<unsigned char*>(b->dtasks[d]) + tb, meta.data(),
+                                      sizeof(p3::BatchMeta) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
         cudaGetLastError();
         return P3_ERR_CUDA;
     }
@@ -246,6 +259,8 @@ static p3_status batch_run_persistent(p3_batch b, int dir, const void* const* in
         L.buf[i][2] = ws ? ws[i] : NULL;
     }
     L.tasks = b->dtasks[dir];
+    L.meta = reinterpret_cast<const p3::BatchMeta*>(reinterpret_cast<const unsigned char*>(b->dtasks[dir]) +
+                                                    sizeof(p3::BatchTask) * std::max<size_t>(1, (size_t)b->ntasks[dir]));
     L.ntasks = b->ntasks[dir];
     L.total = b->total[dir];
     L.ctr = b->dctr[dir];

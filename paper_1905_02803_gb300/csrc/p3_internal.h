@@ -238,8 +238,17 @@ struct BatchTask {
     int dep;            // task that must be finished first, or -1
 };
 constexpr int kBatchMaxPlans = 256;
+// The scheduling fields of a task, in a compact array the CTAs search.
+struct BatchMeta {
+    unsigned first;   // first ticket
+    unsigned ntiles;
+    int dep;          // task that must be finished first, or -1
+    int plan;         // row of the call's buffer table
+    int src, dst;     // buffer roles
+};
 struct BatchLaunch {
     const BatchTask* tasks;  // device array, ntasks entries
+    const BatchMeta* meta;   // device array, ntasks entries
     int ntasks;
     unsigned total;          // tickets
     unsigned* ctr;           // [0] next ticket, [1 + i] finished tiles of task i (zeroed before the launch)

@@ -14,6 +14,8 @@
 // paper's "transpose inside the FFT call" alternative (Sect. 3.3) done in
 // shared memory, replacing the pack / all-to-all / unpack / local-transpose
 // sequence between pencils.
+#include <cstddef>
+
 #include "p3_dft.cuh"
 #include "p3_internal.h"
 
@@ -634,11 +636,16 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
 }
 
 // Batched persistent launch: every CTA takes tickets in order; a ticket is a
-// tile of one (plan, stage) task; the task's arguments are copied to shared
-// memory and the call's buffers filled in; a tile of a later stage first
-// waits (bounded) until every tile of the plan's previous stage finished.
-// A wait that gives up marks *err and skips the tile (the output of that
-// call is invalid), still counting it as finished so no wait behind it hangs.
+// tile of one (plan, stage) task.  Thread 0 claims a CTA's next ticket while
+// the current tile runs (a CTA holds at most one unstarted ticket, larger
+// than its current one, so the smallest unfinished ticket can always
+// proceed), finds its task in the compact scheduling array, and waits
+// (bounded) until every tile of the plan's previous stage finished -- once
+// per task, as a finished stage stays finished.  The task's arguments are
+// copied to shared memory only when the task changes, with the call's
+// buffers filled in.  A wait that gives up marks *err and skips the tile
+// (the output of that call is invalid), still counting it as finished so no
+// wait behind it hangs.
 #ifndef P3_BATCH_MINB
 #define P3_BATCH_MINB P3_GEN_MINB
 #endif
@@ -649,51 +656,61 @@ __global__ void __launch_bounds__(kMaxThreads, P3_BATCH_MINB) batch_kernel(const
     __shared__ long long s_tile;
     __shared__ int s_task, s_ok;
     const int tid = threadIdx.x;
+    int cur = -1;      // task whose arguments sit in sa
+    unsigned next = 0;  // thread 0: the claimed, unstarted ticket
+    int met = -1;       // thread 0: task whose dependency was seen finished
+    if (tid == 0) next = atomicAdd(b.ctr, 1u);
     for (;;) {
         if (tid == 0) {
-            const unsigned tk = atomicAdd(b.ctr, 1u);
-            int task = -1;
+            const unsigned tk = next;
+            int task = -1, ok = 1;
             if (tk < b.total) {
                 int lo = 0, hi = b.ntasks - 1;  // last task with first <= tk
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) / 2;
-                    if (b.tasks[mid].first <= (long long)tk) lo = mid;
+                    if (b.meta[mid].first <= tk) lo = mid;
                     else hi = mid - 1;
                 }
                 task = lo;
-                s_tile = (long long)tk - b.tasks[lo].first;
+                s_tile = (long long)(tk - b.meta[lo].first);
+                next = atomicAdd(b.ctr, 1u);
+                const int dep = b.meta[lo].dep;
+                if (dep >= 0 && met != lo) {
+                    const unsigned need = b.meta[dep].ntiles + b.extra;
+                    unsigned it = 0;
+                    while (ld_acquire_u32(b.ctr + 1 + dep) < need) {
+                        if (++it > b.spin_limit || ld_acquire_u32(b.err) != 0) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                    if (ok) met = lo;
+                    else atomicOr(b.err, 1u);
+                }
             }
             s_task = task;
+            s_ok = ok;
         }
         __syncthreads();
         const int task = s_task;
         if (task < 0) return;
-        {
+        if (task != cur) {
+            // the arguments after the tensor map (unused by the generic
+            // kernel); thread 0 alone writes the buffer pointers
+            constexpr int wb = (int)((offsetof(StageArgs, dst) + sizeof(void*)) / sizeof(int));
+            constexpr int nw = (int)(sizeof(StageArgs) / sizeof(int));
             const int* srcw = reinterpret_cast<const int*>(&b.tasks[task].a);
             int* dstw = reinterpret_cast<int*>(&sa);
-            for (int i = tid; i < (int)(sizeof(StageArgs) / sizeof(int)); i += blockDim.x) dstw[i] = srcw[i];
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const BatchTask& t = b.tasks[task];
-            sa.src = b.buf[t.plan][t.src];
-            sa.dst = b.buf[t.plan][t.dst];
-            int ok = 1;
-            if (t.dep >= 0) {
-                const unsigned need = (unsigned)b.tasks[t.dep].ntiles + b.extra;
-                unsigned it = 0;
-                while (ld_acquire_u32(b.ctr + 1 + t.dep) < need) {
-                    if (++it > b.spin_limit || ld_acquire_u32(b.err) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-                if (!ok) atomicOr(b.err, 1u);
+            for (int i = wb + tid; i < nw; i += blockDim.x) dstw[i] = srcw[i];
+            if (tid == 0) {
+                const BatchMeta& m = b.meta[task];
+                sa.src = b.buf[m.plan][m.src];
+                sa.dst = b.buf[m.plan][m.dst];
             }
-            s_ok = ok;
+            __syncthreads();
+            cur = task;
         }
-        __syncthreads();
         if (s_ok) stage_tile<float>(sa, s_tile, smem_raw);
         __syncthreads();
         if (tid == 0) {
