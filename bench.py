@@ -597,6 +597,9 @@ REPORT_CONFIGS = [
     ("channel_480x360x257_f64", (480, 360, 257), "f64", ("fft", "fft", "cheb"), "zyx", "channel"),
     ("sine_512x512x255_f32", (512, 512, 255), "f32", ("fft", "fft", "sine"), "zyx", "turbulence"),
     ("inplace_512cube_f32_xyz", (512, 512, 512), "f32", ("fft", "fft", "fft"), "xyz", "turbulence", "inplace"),
+    # the generic mixed-radix kernel: an even 7-smooth grid, and odd X rows in pairs
+    ("smooth_384cube_f32", (384, 384, 384), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
+    ("odd_375x360x343_f32", (375, 360, 343), "f32", ("fft", "fft", "fft"), "zyx", "turbulence"),
 ]
 
 
