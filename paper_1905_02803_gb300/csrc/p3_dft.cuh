@@ -1,5 +1,6 @@
 // Complex helpers and forward DFT butterflies (exp(-2 pi i n m / R)) of
-// sizes 2, 3, 4, 5, 7, 8, 16 and 32 on registers, shared by the stage kernels.
+// sizes 2, 3, 4, 5, 7, 8, 16 and 32 on registers, and of the composite sizes
+// 6 .. 28 built from them, shared by the stage kernels.
 // The inverse-sign DFT is swp(DFT(swp(x))), so only the forward form exists.
 #pragma once
 
@@ -264,5 +265,126 @@ template <class C, class T> struct Dft<C, T, 5> {
 template <class C, class T> struct Dft<C, T, 7> {
     static __device__ __forceinline__ void run(C* v) { DftOdd<C, T, 7>::run(v); }
 };
+
+// ---------------------------------------------------------------------------
+// Compile-time cos / sin of 2 pi m / n (the composite butterflies' internal
+// twiddles): the angle is reduced to the first octant, where the Taylor
+// series of sin and cos converge to double precision within 13 terms
+// (x <= pi/4: x^26 / 26! < 1e-28).
+// ---------------------------------------------------------------------------
+struct KTrigVal {
+    double c, s;
+};
+__host__ __device__ constexpr KTrigVal ksincos_octant(double x)  // 0 <= x <= pi/4
+{
+    double c = 0.0, s = 0.0, tc = 1.0, ts = x;
+    for (int k = 0; k < 13; ++k) {
+        c += tc;
+        s += ts;
+        tc *= -x * x / ((2.0 * k + 1.0) * (2.0 * k + 2.0));
+        ts *= -x * x / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+    return KTrigVal{c, s};
+}
+__host__ __device__ constexpr KTrigVal ktrig2pi(long long m, long long n)
+{
+    constexpr double pi4 = 0.78539816339744830962;  // pi / 4
+    m %= n;
+    if (m < 0) m += n;
+    const long long o = (8 * m) / n;      // octant
+    const long long r = 8 * m - o * n;    // angle = (pi/4) (o + r/n)
+    double c = 0.0, s = 0.0;
+    if ((o & 1) == 0) {
+        const KTrigVal t = ksincos_octant(pi4 * (double)r / (double)n);
+        switch (o / 2) {
+        case 0: c = t.c; s = t.s; break;
+        case 1: c = -t.s; s = t.c; break;
+        case 2: c = -t.c; s = -t.s; break;
+        default: c = t.s; s = -t.c; break;
+        }
+    } else {
+        const KTrigVal t = ksincos_octant(pi4 * (double)(n - r) / (double)n);  // (o+1) pi/4 - angle
+        switch ((o + 1) / 2) {
+        case 1: c = t.s; s = t.c; break;
+        case 2: c = -t.c; s = t.s; break;
+        case 3: c = -t.s; s = -t.c; break;
+        default: c = t.c; s = -t.s; break;
+        }
+    }
+    return KTrigVal{c, s};
+}
+template <int N> struct KTrigTab {
+    double c[N], s[N];
+};
+template <int N> __host__ __device__ constexpr KTrigTab<N> ktrig_tab()
+{
+    KTrigTab<N> t{};
+    for (int m = 0; m < N; ++m) {
+        const KTrigVal v = ktrig2pi(m, N);
+        t.c[m] = v.c;
+        t.s[m] = v.s;
+    }
+    return t;
+}
+
+// a * exp(-2 pi i m / R) for a compile-time m (after unrolling): exact for
+// the multiples of a quarter turn
+template <class C, class T, int R>
+__device__ __forceinline__ C twiddle_const(C a, int m, const KTrigTab<R>& tw)
+{
+    if (m == 0) return a;
+    if (4 * m == R) return mmi(a);                      // -i
+    if (2 * m == R) return mk<C>(-a.x, -a.y);           // -1
+    if (4 * m == 3 * R) return mk<C>(-a.y, a.x);        // +i
+    return rot(a, (T)tw.c[m], (T)-tw.s[m]);
+}
+
+// Composite size R = R1 R2 on registers (Cooley-Tukey with n = R2 n1 + n2,
+// k = k1 + R1 k2): R2 DFTs of size R1 over the inputs n2, n2 + R2, ...,
+// the internal twiddles exp(-2 pi i n2 k1 / R), then R1 DFTs of size R2.
+template <class C, class T, int R1, int R2> struct DftCT {
+    static constexpr int R = R1 * R2;
+    static __device__ __forceinline__ void run(C* v)
+    {
+        constexpr KTrigTab<R> tw = ktrig_tab<R>();
+        C y[R];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            C a[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[R2 * n1 + n2];
+            Dft<C, T, R1>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) y[n2 * R1 + k1] = twiddle_const<C, T, R>(a[k1], (n2 * k1) % R, tw);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            C b[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) b[n2] = y[n2 * R1 + k1];
+            Dft<C, T, R2>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+        }
+    }
+};
+#define P3_DFT_CT(R, R1, R2)                                            \
+    template <class C, class T> struct Dft<C, T, R> {                   \
+        static __device__ __forceinline__ void run(C* v) { DftCT<C, T, R1, R2>::run(v); } \
+    };
+P3_DFT_CT(6, 2, 3)
+P3_DFT_CT(9, 3, 3)
+P3_DFT_CT(10, 2, 5)
+P3_DFT_CT(12, 4, 3)
+P3_DFT_CT(14, 2, 7)
+P3_DFT_CT(15, 3, 5)
+P3_DFT_CT(18, 2, 9)
+P3_DFT_CT(20, 4, 5)
+P3_DFT_CT(21, 3, 7)
+P3_DFT_CT(24, 8, 3)
+P3_DFT_CT(25, 5, 5)
+P3_DFT_CT(27, 3, 9)
+P3_DFT_CT(28, 4, 7)
+#undef P3_DFT_CT
 
 }  // namespace p3

@@ -18,6 +18,15 @@ constexpr int kMaxPasses = 14;
 #define P3_GEN_VMAX 16
 #endif
 constexpr int kVmax = P3_GEN_VMAX;
+// Largest composite radix (register butterflies 6 .. 28) of the FP32 generic
+// kernel; the plan's factorisation uses the same bound.  16 (composites 6, 9,
+// 10, 12, 14, 15) keeps the kernel free of spills at 85 registers and
+// measured best on the 64-grid batch (6.89 ms, against 7.15 ms with all
+// composites up to 28, whose larger butterflies spill).
+#ifndef P3_GEN_MAXCR
+#define P3_GEN_MAXCR 16
+#endif
+constexpr int kMaxCompositeRadix = P3_GEN_MAXCR;
 // Threads per CTA never exceed this (matches __launch_bounds__).
 constexpr int kMaxThreads = 256;
 // Threads per CTA of the generic stage kernel (its own launch bounds).

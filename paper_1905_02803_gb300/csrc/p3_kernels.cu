@@ -84,7 +84,27 @@ __device__ __forceinline__ void pass_any(int R, const C* src, C* dst, int LDB, i
     case 3: pass_pp<C, T, 3, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
     case 5: pass_pp<C, T, 5, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
     case 7: pass_pp<C, T, 7, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
-    default: break;
+    default:
+        // composite radices (FP32 plans only; see the plan's factorisation)
+        if constexpr (sizeof(T) == 4) {
+            switch (R) {
+            case 6: if constexpr (6 <= P3_GEN_MAXCR) pass_pp<C, T, 6, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 9: if constexpr (9 <= P3_GEN_MAXCR) pass_pp<C, T, 9, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 10: if constexpr (10 <= P3_GEN_MAXCR) pass_pp<C, T, 10, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 12: if constexpr (12 <= P3_GEN_MAXCR) pass_pp<C, T, 12, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 14: if constexpr (14 <= P3_GEN_MAXCR) pass_pp<C, T, 14, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 15: if constexpr (15 <= P3_GEN_MAXCR) pass_pp<C, T, 15, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 18: if constexpr (18 <= P3_GEN_MAXCR) pass_pp<C, T, 18, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 20: if constexpr (20 <= P3_GEN_MAXCR) pass_pp<C, T, 20, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 21: if constexpr (21 <= P3_GEN_MAXCR) pass_pp<C, T, 21, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 24: if constexpr (24 <= P3_GEN_MAXCR) pass_pp<C, T, 24, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 25: if constexpr (25 <= P3_GEN_MAXCR) pass_pp<C, T, 25, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 27: if constexpr (27 <= P3_GEN_MAXCR) pass_pp<C, T, 27, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            case 28: if constexpr (28 <= P3_GEN_MAXCR) pass_pp<C, T, 28, SWAP>(src, dst, LDB, l, t, tpl, n, Ns, c, tw); break;
+            default: break;
+            }
+        }
+        break;
     }
 }
 

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <complex>
+#include <functional>
 #include <map>
 #include <new>
 #include <string>
@@ -144,12 +145,63 @@ void host_dft_pow2(std::vector<std::complex<long double>>& a)
     }
 }
 
-// Radix sequence for n (16s first, then 8/4/2, then 3, 5, 7).  Returns false
-// when n has a prime factor above 7.
-bool factor(int n, std::vector<int>& rad)
+// FP32 generic stages factor their lengths into composite radices (1) or
+// the native ones only (0).
+#ifndef P3_GEN_COMPOSITE
+#define P3_GEN_COMPOSITE 1
+#endif
+// Radix sequence for n (16s first, then 8/4/2, then 3, 5, 7).  With
+// composite = true (FP32 plans) and a factor 3, 5 or 7 in n, the sequence
+// instead takes the fewest passes from the native radices and the composite
+// register butterflies 6 .. 28, ties going to the one whose smallest radix is
+// largest, largest radix first.  Returns false when n has a prime factor
+// above 7.
+bool factor(int n, std::vector<int>& rad, bool composite = false)
 {
     rad.clear();
     int m = n;
+    int e2 = 0, e3 = 0, e5 = 0, e7 = 0;
+    while (m > 1 && m % 2 == 0) { m /= 2; ++e2; }
+    while (m > 1 && m % 3 == 0) { m /= 3; ++e3; }
+    while (m > 1 && m % 5 == 0) { m /= 5; ++e5; }
+    while (m > 1 && m % 7 == 0) { m /= 7; ++e7; }
+    if (m != 1) return false;
+    if (composite && e3 + e5 + e7 > 0) {
+        // radices as exponent vectors (2, 3, 5, 7)
+        static const int kRad[][5] = {
+            {28, 2, 0, 0, 1}, {27, 0, 3, 0, 0}, {25, 0, 0, 2, 0}, {24, 3, 1, 0, 0}, {21, 0, 1, 0, 1},
+            {20, 2, 0, 1, 0}, {18, 1, 2, 0, 0}, {16, 4, 0, 0, 0}, {15, 0, 1, 1, 0}, {14, 1, 0, 0, 1},
+            {12, 2, 1, 0, 0}, {10, 1, 0, 1, 0}, {9, 0, 2, 0, 0},  {8, 3, 0, 0, 0},  {7, 0, 0, 0, 1},
+            {6, 1, 1, 0, 0},  {5, 0, 0, 1, 0},  {4, 2, 0, 0, 0},  {3, 0, 1, 0, 0},  {2, 1, 0, 0, 0}};
+        struct Best {
+            int passes, minr;
+            std::vector<int> seq;
+        };
+        std::map<long long, Best> memo;
+        std::function<Best(int, int, int, int)> best = [&](int a, int b, int c, int d) -> Best {
+            if (a + b + c + d == 0) return Best{0, 1 << 30, {}};
+            const long long key = (((long long)a * 64 + b) * 64 + c) * 64 + d;
+            auto it = memo.find(key);
+            if (it != memo.end()) return it->second;
+            Best r{1 << 30, 0, {}};
+            for (const auto& k : kRad) {
+                if (k[1] > a || k[2] > b || k[3] > c || k[4] > d) continue;
+                if (k[0] > p3::kMaxCompositeRadix && k[0] != 16) continue;
+                Best t = best(a - k[1], b - k[2], c - k[3], d - k[4]);
+                const int passes = t.passes + 1, minr = std::min(t.minr, k[0]);
+                if (passes < r.passes || (passes == r.passes && minr > r.minr)) {
+                    t.seq.push_back(k[0]);
+                    r = Best{passes, minr, t.seq};
+                }
+            }
+            memo[key] = r;
+            return r;
+        };
+        rad = best(e2, e3, e5, e7).seq;
+        std::sort(rad.begin(), rad.end(), std::greater<int>());
+        return (int)rad.size() <= p3::kMaxPasses;
+    }
+    m = n;
     while (m % 16 == 0) { rad.push_back(16); m /= 16; }
     if (m % 8 == 0) { rad.push_back(8); m /= 8; }
     if (m % 4 == 0) { rad.push_back(4); m /= 4; }
@@ -160,11 +212,18 @@ bool factor(int n, std::vector<int>& rad)
 }
 
 // Threads per line of the generic kernel: each thread takes about kVmax
-// values per pass (the passes loop over butterflies, so any count works).
+// values per pass (the passes loop over butterflies, so any count works);
+// with P3_GEN_TPL_MAXR, at least the largest radix's worth, so that the
+// passes of a composite radix above kVmax keep every thread busy.
+#ifndef P3_GEN_TPL_MAXR
+#define P3_GEN_TPL_MAXR 0
+#endif
 int threads_per_line(int n, const std::vector<int>& rad)
 {
-    (void)rad;
-    int tpl = (n + p3::kVmax - 1) / p3::kVmax;
+    int vmax = p3::kVmax;
+    if (P3_GEN_TPL_MAXR)
+        for (int r : rad) vmax = std::max(vmax, r);
+    int tpl = (n + vmax - 1) / vmax;
     if (tpl < 1) tpl = 1;
     if (tpl > p3::kMaxThreads) tpl = p3::kMaxThreads;
     return tpl;
@@ -263,7 +322,7 @@ struct Pending {
 
 // Line-FFT set-up: native radices over nfft, else Bluestein over m.
 // Returns P3_ERR_UNSUPPORTED for lines beyond the shared-memory limit.
-p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
+p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native, bool composite)
 {
     std::vector<int> rad;
     a.blue = 0;
@@ -274,7 +333,7 @@ p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native)
         a.tpl = 1;
         return P3_OK;
     }
-    if (factor(a.nfft, rad)) {
+    if (factor(a.nfft, rad, composite)) {
         if (a.nfft > p3::kMaxLine) return P3_ERR_UNSUPPORTED;
         a.npass = (int)rad.size();
         for (int i = 0; i < a.npass; ++i) a.rad[i] = rad[i];
@@ -698,7 +757,7 @@ p3_status p3_plan_create(p3_plan* out, int nx, int ny, int nz, p3_precision prec
             pd.tw2 = roots_table(T, NX) + 1;
         }
         if (a.op != p3::OP_COPY) {
-            rc = line_setup(a, pd, T, twn);
+            rc = line_setup(a, pd, T, twn, prec == P3_F32 && P3_GEN_COMPOSITE);
             if (rc != P3_OK) return;
             // row-style twiddles for power-of-two lines (E as the row kernels take it)
             const long long n = a.nfft;
