@@ -62,6 +62,38 @@ def test_bluestein_lengths(shape, prec):
         assert ef <= TOL[prec] and eb <= TOL[prec], (layout, ef, eb)
 
 
+# FP32 generic stages factor lengths with a factor 3, 5 or 7 into the fewest
+# passes over the native radices and the composite register butterflies 6,
+# 9, 10, 12, 14 and 15; FP64 stages keep the native radices.  Each composite
+# appears in one of these plans (Y and Z lengths; X half-lengths of even Nx).
+COMPOSITE_CASES = [
+    ((12, 54, 100), {"6", "9", "10"}),     # X 6; Y 54 = 9 x 6; Z 100 = 10 x 10
+    ((30, 14, 135), {"15", "14", "9"}),    # X 15; Y 14; Z 135 = 15 x 9
+    ((24, 96, 225), {"12", "8", "15"}),    # X 12; Y 96 = 12 x 8; Z 225 = 15 x 15
+]
+
+
+@pytest.mark.parametrize("shape,radices", COMPOSITE_CASES)
+@pytest.mark.parametrize("layout", ["zyx", "xyz"])
+def test_composite_radices(shape, radices, layout):
+    nx, ny, nz = shape
+    ef, eb, plan = check_case(nx, ny, nz, "f32", layout=layout, seed=nx + nz)
+    used = set()
+    for line in plan.describe().splitlines():
+        for w in line.split():
+            if w.startswith("radices="):
+                used.update(w[len("radices="):].split("x"))
+    assert radices <= used, (radices, used)
+    assert ef <= TOL["f32"] and eb <= TOL["f32"], (ef, eb)
+    # the same grid in FP64 keeps the native radices 2, 3, 4, 5, 7, 8, 16
+    ef64, eb64, plan64 = check_case(nx, ny, nz, "f64", layout=layout, seed=nx + nz)
+    for line in plan64.describe().splitlines():
+        for w in line.split():
+            if w.startswith("radices="):
+                assert set(w[len("radices="):].split("x")) <= {"2", "3", "4", "5", "7", "8", "16"}, line
+    assert ef64 <= TOL["f64"] and eb64 <= TOL["f64"], (ef64, eb64)
+
+
 @pytest.mark.parametrize("ttypes", [("fft", "fft", "cheb"), ("fft", "empty", "cheb"), ("fft", "empty", "empty"),
                                     ("fft", "fft", "empty"), ("fft", "empty", "fft"), ("fft", "fft", "sine"),
                                     ("fft", "empty", "sine")])
