@@ -211,6 +211,20 @@ bool factor(int n, std::vector<int>& rad, bool composite = false)
     return m == 1 && (int)rad.size() <= p3::kMaxPasses;
 }
 
+// Every radix has a butterfly in the generic kernel of the plan's precision
+// (a pass of any other radix would be skipped there).
+bool radices_supported(const std::vector<int>& rad, bool composite)
+{
+    for (int r : rad) {
+        const bool native = r == 2 || r == 3 || r == 4 || r == 5 || r == 7 || r == 8 || r == 16;
+        const bool comp = composite && r <= p3::kMaxCompositeRadix &&
+                          (r == 6 || r == 9 || r == 10 || r == 12 || r == 14 || r == 15 || r == 18 || r == 20 ||
+                           r == 21 || r == 24 || r == 25 || r == 27 || r == 28);
+        if (!native && !comp) return false;
+    }
+    return true;
+}
+
 // Threads per line of the generic kernel: each thread takes about kVmax
 // values per pass (the passes loop over butterflies, so any count works);
 // with P3_GEN_TPL_MAXR, at least the largest radix's worth, so that the
@@ -335,6 +349,7 @@ p3_status line_setup(StageArgs& a, Pending& pend, TableSet& T, int twn_native, b
     }
     if (factor(a.nfft, rad, composite)) {
         if (a.nfft > p3::kMaxLine) return P3_ERR_UNSUPPORTED;
+        if (!radices_supported(rad, composite)) return P3_ERR_UNSUPPORTED;
         a.npass = (int)rad.size();
         for (int i = 0; i < a.npass; ++i) a.rad[i] = rad[i];
         a.tpl = threads_per_line(a.nfft, rad);
