@@ -205,6 +205,21 @@ p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len);
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches);
 
 /*
+ * The radix sequence a plan of precision prec gives the generic-kernel
+ * stages of a line of n points (the Cooley-Tukey factorisation behind each
+ * 1D FFT of Sect. 2; no device work, no GPU needed).  FP32 lengths with a
+ * factor 3, 5 or 7 take the fewest passes over the native radices 2, 3, 4,
+ * 5, 7, 8, 16 and the composite register butterflies up to 15; other
+ * lengths take 16s first, then 8 / 4 / 2, then 3, 5, 7.  radices receives
+ * up to cap entries (the largest radix first), *npass their count.
+ * P3_ERR_UNSUPPORTED when n has a prime factor above 7 (such lines run
+ * Bluestein's algorithm over a power-of-two length) or the sequence is
+ * longer than cap; P3_ERR_INVALID for n < 2, a bad precision or NULL
+ * pointers.
+ */
+p3_status p3_plan_factor(int n, p3_precision prec, int* radices, int cap, int* npass);
+
+/*
  * Plane-fused X + Y launches (no paper counterpart; see P3_FLAG_NO_FUSE):
  * their CTAs wait, with a bounded number of polls, for the tiles of the same
  * z-plane that other CTAs compute.  A wait that gives up marks the plan's

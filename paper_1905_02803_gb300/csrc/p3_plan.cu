@@ -1309,6 +1309,18 @@ p3_status p3_plan_describe(p3_plan plan, char* buf, size_t len)
     return P3_OK;
 }
 
+p3_status p3_plan_factor(int n, p3_precision prec, int* radices, int cap, int* npass)
+{
+    if (n < 2 || !radices || !npass || cap < 1 || (prec != P3_F32 && prec != P3_F64)) return P3_ERR_INVALID;
+    const bool composite = prec == P3_F32 && P3_GEN_COMPOSITE;
+    std::vector<int> rad;
+    if (!factor(n, rad, composite) || !radices_supported(rad, composite)) return P3_ERR_UNSUPPORTED;
+    if ((int)rad.size() > cap) return P3_ERR_UNSUPPORTED;
+    for (size_t i = 0; i < rad.size(); ++i) radices[i] = rad[i];
+    *npass = (int)rad.size();
+    return P3_OK;
+}
+
 p3_status p3_plan_launches(p3_plan plan, int dir, int* launches)
 {
     if (!plan || !launches || (dir != 0 && dir != 1)) return P3_ERR_INVALID;

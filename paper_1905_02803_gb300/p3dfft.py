@@ -29,7 +29,7 @@ P3_WAIT_FUSED_QUEUE, P3_WAIT_COPY = 1, 2
 EXPORTS = ("p3_plan_create", "p3_plan_destroy", "p3_ftran_r2c", "p3_btran_c2r", "p3_ftran_r2c_noalloc",
            "p3_plan_get_dims",
            "p3_plan_workspace_bytes", "p3_plan_scale", "p3_plan_set_stage_events", "p3_plan_describe",
-           "p3_plan_launches", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_wait_flags",
+           "p3_plan_launches", "p3_plan_factor", "p3_plan_set_z_hook", "p3_plan_wait_status", "p3_plan_wait_flags",
            "p3_plan_set_wait_limits",
            "p3_plan_set_fused_lag", "p3_batch_create", "p3_batch_destroy", "p3_batch_ftran_r2c",
            "p3_batch_btran_c2r", "p3_batch_wait_status", "p3_batch_set_wait_limits", "p3_batch_launches",
@@ -70,6 +70,7 @@ def load():
     lib.p3_plan_set_stage_events.argtypes = [P, ctypes.POINTER(P), I]
     lib.p3_plan_describe.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     lib.p3_plan_launches.argtypes = [P, I, ctypes.POINTER(I)]
+    lib.p3_plan_factor.argtypes = [I, I, ctypes.POINTER(I), I, ctypes.POINTER(I)]
     lib.p3_plan_set_z_hook.argtypes = [P, Z_HOOK, P]
     lib.p3_plan_wait_status.argtypes = [P]
     lib.p3_plan_wait_flags.argtypes = [P, ctypes.POINTER(U)]
@@ -268,6 +269,19 @@ def p3_plan_describe(plan) -> str:
     buf = ctypes.create_string_buffer(1 << 14)
     _check(load().p3_plan_describe(plan, buf, len(buf)), "p3_plan_describe")
     return buf.value.decode()
+
+
+def p3_plan_factor(n: int, precision: str = "f32"):
+    """Radix sequence of the generic-kernel stages of an n-point line (no GPU
+    needed); None when n has a prime factor above 7."""
+    prec = {"f32": P3_F32, "f64": P3_F64}[precision]
+    buf = (ctypes.c_int * 32)()
+    cnt = ctypes.c_int()
+    rc = load().p3_plan_factor(int(n), prec, buf, 32, ctypes.byref(cnt))
+    if rc == P3_ERR_UNSUPPORTED:
+        return None
+    _check(rc, "p3_plan_factor")
+    return [buf[i] for i in range(cnt.value)]
 
 
 def p3_plan_launches(plan, direction: int) -> int:
