@@ -346,6 +346,12 @@ __device__ __forceinline__ void pair_store(const StageArgs& a, const C* sl, int 
     }
 }
 
+// X stages whose rows lie one after another walk each tile's values as one
+// run (1), or row by row with a warp per row (0).
+#ifndef P3_GEN_FLAT
+#define P3_GEN_FLAT 1
+#endif
+
 // Ops whose load is a plain copy of one complex value (no pre-processing
 // beyond the inverse's real/imaginary swap): their tiles are filled by
 // asynchronous copies straight into shared memory, all of a thread's copies
@@ -490,19 +496,42 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
         const int e0 = ef ? tid & 31 : tid >> lb, de = ef ? 32 : NT >> lb;
         const long long gstep = (long long)de * (a.op == OP_R2C_HALF ? 1 : a.in.es);  // complex values
         const unsigned sstep = (unsigned)(de * LDB * (int)sizeof(C));
-        for (int l = l0; l < B; l += dl) {
-            const long long L = L0 + l;
-            if (L >= a.nlines) break;
-            const long long base = line_base(a.in, L);
-            const C* g = direct_src<C, T>(a, base, e0);
-            unsigned sa = (unsigned)__cvta_generic_to_shared(s0 + e0 * LDB + l);
-            for (int e = e0; e < nload; e += de) {
-                copy_async(sa, g);
-                g += gstep;
-                sa += sstep;
+        // X rows stored one after another: the tile is one contiguous run
+        // of its rows' complex values, which all threads walk together
+        const int rowc = a.op == OP_C2R_HALF ? nload + 1 : nload;  // complex values per input row
+        if (P3_GEN_FLAT && ef && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) && a.in.per >= a.nlines &&
+            a.in.lstride == (a.op == OP_R2C_HALF ? 2LL * nload : (long long)rowc)) {
+            const long long rows = a.nlines - L0 < B ? a.nlines - L0 : B;
+            const int total = (int)rows * rowc;
+            const long long b0 = line_base(a.in, L0);
+            const C* g0 = a.op == OP_R2C_HALF ? reinterpret_cast<const C*>(static_cast<const T*>(a.src) + b0)
+                                              : static_cast<const C*>(a.src) + b0;
+            int l = tid / rowc, e = tid - l * rowc;  // element i = l * rowc + e
+            const int dq = NT / rowc, dr = NT - dq * rowc;
+            for (int i = tid; i < total; i += NT) {
+                copy_async((unsigned)__cvta_generic_to_shared(e < nload ? s0 + e * LDB + l : s1 + l), g0 + i);
+                e += dr;
+                l += dq;
+                if (e >= rowc) {
+                    e -= rowc;
+                    ++l;
+                }
             }
-            if (a.op == OP_C2R_HALF && e0 == 0)
-                copy_async((unsigned)__cvta_generic_to_shared(s1 + l), direct_src<C, T>(a, base, nload));
+        } else {
+            for (int l = l0; l < B; l += dl) {
+                const long long L = L0 + l;
+                if (L >= a.nlines) break;
+                const long long base = line_base(a.in, L);
+                const C* g = direct_src<C, T>(a, base, e0);
+                unsigned sa = (unsigned)__cvta_generic_to_shared(s0 + e0 * LDB + l);
+                for (int e = e0; e < nload; e += de) {
+                    copy_async(sa, g);
+                    g += gstep;
+                    sa += sstep;
+                }
+                if (a.op == OP_C2R_HALF && e0 == 0)
+                    copy_async((unsigned)__cvta_generic_to_shared(s1 + l), direct_src<C, T>(a, base, nload));
+            }
         }
         copy_async_wait();
         if (sw_in && a.npass == 0) {
@@ -596,7 +625,48 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     }
 
     // ---- store: shared memory -> HBM -----------------------------------
-    {
+    // X rows stored one after another: all threads walk the tile's output
+    // values together (R2C: H bins per row; C2R: n real pairs per row)
+    if (P3_GEN_FLAT && a.out_elem_fast && !a.blue && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) &&
+        a.out.per >= a.nlines && a.out.lstride == (a.op == OP_R2C_HALF ? (long long)a.n_out : 2LL * a.n_out)) {
+        const int rowo = a.n_out;
+        const long long rows = a.nlines - L0 < B ? a.nlines - L0 : B;
+        const int total = (int)rows * rowo;
+        const long long b0 = line_base(a.out, L0);
+        int l = tid / rowo, e = tid - l * rowo;  // element i = l * rowo + e
+        const int dq = NT / rowo, dr = NT - dq * rowo;
+        if (a.op == OP_R2C_HALF) {
+            // F[k] = (Z[k] + conj Z[n-k]) / 2 - i exp(-2 pi i k / Nx) (Z[k] - conj Z[n-k]) / 2
+            const int n = a.nfft;
+            const C* tw2 = static_cast<const C*>(a.tw2);
+            C* g0 = static_cast<C*>(a.dst) + b0;
+            for (int i = tid; i < total; i += NT) {
+                const C* sl = s + l;
+                const C zk = sl[(e == n ? 0 : e) * LDB];
+                const C zm = cnj(sl[(e == 0 ? 0 : n - e) * LDB]);
+                const C q = mul(ldg(tw2 + e), sub(zk, zm));
+                g0[i] = mk<C>((T)0.5 * (zk.x + zm.x + q.y), (T)0.5 * (zk.y + zm.y - q.x));
+                e += dr;
+                l += dq;
+                if (e >= rowo) {
+                    e -= rowo;
+                    ++l;
+                }
+            }
+        } else {
+            // f[2j] = Re z[j], f[2j+1] = Im z[j]: one complex-sized store per j
+            C* g0 = reinterpret_cast<C*>(static_cast<T*>(a.dst) + b0);
+            for (int i = tid; i < total; i += NT) {
+                g0[i] = swp(s[e * LDB + l]);
+                e += dr;
+                l += dq;
+                if (e >= rowo) {
+                    e -= rowo;
+                    ++l;
+                }
+            }
+        }
+    } else {
         const bool ef = a.out_elem_fast;
         const int l0 = ef ? tid >> 5 : tid & (B - 1), dl = ef ? NT >> 5 : B;
         const int e0 = ef ? tid & 31 : tid >> lb, de = ef ? 32 : NT >> lb;
