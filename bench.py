@@ -77,16 +77,21 @@ def fp64_ops_record(config):
             rec = json.load(f)
     except Exception:
         return None
+    ent = rec.get("configs", {}).get(config)
+    if ent is None:
+        return None
+    # a configuration may name the sources of its own kernels
+    srcs = ent.get("kernel_sources", rec.get("kernel_sources", []))
+    want = ent.get("kernel_source_sha256_16", rec.get("kernel_source_sha256_16"))
     h = hashlib.sha256()
-    for rel in rec.get("kernel_sources", []):
+    for rel in srcs:
         try:
             h.update(open(os.path.join(ROOT, rel), "rb").read())
         except OSError:
             return None
-    if not rec.get("kernel_sources") or rec.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+    if not srcs or want != h.hexdigest()[:16]:
         return None
-    ent = rec.get("configs", {}).get(config)
-    return None if ent is None else (float(ent["fp64_flop_per_pair"]), float(ent["fp64_inst_per_pair"]))
+    return float(ent["fp64_flop_per_pair"]), float(ent["fp64_inst_per_pair"])
 
 
 def stage_model_bytes(nx, ny, nz, e):

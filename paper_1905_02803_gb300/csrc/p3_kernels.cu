@@ -346,8 +346,9 @@ __device__ __forceinline__ void pair_store(const StageArgs& a, const C* sl, int 
     }
 }
 
-// X stages whose rows lie one after another walk each tile's values as one
-// run (1), or row by row with a warp per row (0).
+// FP32 X stages whose rows lie one after another walk each tile's values as
+// one run (1), or row by row with a warp per row (0).  FP64 stages, bound by
+// the FP64 pipe, keep the row-by-row walk.
 #ifndef P3_GEN_FLAT
 #define P3_GEN_FLAT 1
 #endif
@@ -499,7 +500,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
         // X rows stored one after another: the tile is one contiguous run
         // of its rows' complex values, which all threads walk together
         const int rowc = a.op == OP_C2R_HALF ? nload + 1 : nload;  // complex values per input row
-        if (P3_GEN_FLAT && ef && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) && a.in.per >= a.nlines &&
+        if (P3_GEN_FLAT && sizeof(T) == 4 && ef && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) && a.in.per >= a.nlines &&
             a.in.lstride == (a.op == OP_R2C_HALF ? 2LL * nload : (long long)rowc)) {
             const long long rows = a.nlines - L0 < B ? a.nlines - L0 : B;
             const int total = (int)rows * rowc;
@@ -627,7 +628,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long long tile, u
     // ---- store: shared memory -> HBM -----------------------------------
     // X rows stored one after another: all threads walk the tile's output
     // values together (R2C: H bins per row; C2R: n real pairs per row)
-    if (P3_GEN_FLAT && a.out_elem_fast && !a.blue && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) &&
+    if (P3_GEN_FLAT && sizeof(T) == 4 && a.out_elem_fast && !a.blue && (a.op == OP_R2C_HALF || a.op == OP_C2R_HALF) &&
         a.out.per >= a.nlines && a.out.lstride == (a.op == OP_R2C_HALF ? (long long)a.n_out : 2LL * a.n_out)) {
         const int rowo = a.n_out;
         const long long rows = a.nlines - L0 < B ? a.nlines - L0 : B;
